@@ -1,0 +1,193 @@
+/*
+ * hd.h -- C ABI of the GB300 one-step overlapping DDM Helmholtz solver.
+ *
+ * Method: Leng & Ju, "An overlapping domain decomposition preconditioner for
+ * the Helmholtz equation" (arXiv 1508.02897).  The 2D Helmholtz problem
+ * Delta u + k^2 u = f (Eq. (helm)) is truncated by a uniaxial PML (Sec. 2,
+ * Eq. (pml)) and discretised by a conservative second-order 5-point stencil
+ * (Sec. 3).  GMRES (Sec. 3) is preconditioned by the one-step DDM
+ * preconditioner of Eq. (ddm0) and Eq. (pc): restrict the residual to every
+ * owned box, solve every local PML problem of Eq. (pmlij) at once, and add
+ * every full local solution, including its PML area, back into the global
+ * vector.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an hd_status (HD_OK = 0); hd_last_error() gives a
+ *    message for the calling thread.  No C++ exception crosses this boundary.
+ *  - Grid: interior nx x ny cells of width h plus npml PML cells on every side;
+ *    the global grid is NX = nx + 2 npml by NY = ny + 2 npml, stored row by row
+ *    (x fastest).  A complex vector is interleaved double re/im
+ *    (C99 double _Complex / numpy complex128) of NX*NY entries per right-hand
+ *    side; several right-hand sides are stored one after another.
+ *  - Pointers named *_dev are device pointers owned by the caller; the library
+ *    never frees them.  Workspaces are sized by hd_query_workspace and allocated
+ *    by the caller (for instance with torch.empty on the device).
+ *  - `stream` is a cudaStream_t passed as void*.  Calls are asynchronous on it
+ *    unless stated otherwise.
+ *  - A context is not thread safe: one host thread per context at a time.
+ */
+#ifndef HD_H_
+#define HD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HD_OK = 0,
+  HD_ERR_INVALID = 1,        /* bad argument, size or state                      */
+  HD_ERR_OOM = 2,            /* a workspace is too small / allocation failed     */
+  HD_ERR_CUDA = 3,           /* a CUDA runtime call failed                        */
+  HD_ERR_NOT_CONVERGED = 4,  /* GMRES hit max_iters (stats are still filled in)   */
+  HD_ERR_NUMERIC = 5,        /* NaN/Inf or a zero pivot                           */
+  HD_ERR_TIMEOUT = 6,        /* a bounded device wait gave up                      */
+  HD_PENDING = 7             /* reserved for asynchronous request handles          */
+} hd_status;
+
+typedef enum {
+  HD_C128 = 0,  /* local factors and substitutions in complex FP64              */
+  HD_C64 = 1    /* local factors and substitutions in complex FP32, FP64 outside */
+} hd_precision;
+
+/* Truncated domain Omega of Sec. 2: interior nx x ny cells of width h (the
+ * interior is [0, nx h] x [0, ny h]), npml PML cells per side.  The PML uses
+ * alpha(xi) = 1 + i sigma(xi)/omega with sigma(xi)/omega =
+ * sigma0_over_omega * (xi / (npml h))^pml_power, xi the distance into the layer. */
+typedef struct {
+  int32_t nx, ny, npml;
+  double h;
+  double omega;
+  double sigma0_over_omega;
+  int32_t pml_power;
+} hd_grid;
+
+/* Decomposition of Sec. 2 (Fig. 1): nbx x nby owned boxes cut at the interior
+ * cut points cut_x[0..nbx] (cut_x[0] = npml, cut_x[nbx] = npml + nx; NULL =
+ * even cuts), likewise cut_y; each box is extended by `overlap` cells (lo) plus
+ * npml local PML cells on its inner sides and by npml cells on its outer sides.
+ * own_global_pml = 1 lets the boundary boxes also own the adjacent global-PML
+ * cells so the owned boxes tile the whole grid; 0 is the literal reading
+ * (owned boxes tile the interior only).  Every owned width must be at least
+ * overlap + npml.  The arrays are copied; the caller keeps ownership. */
+typedef struct {
+  int32_t nbx, nby, overlap;
+  const int32_t *cut_x;
+  const int32_t *cut_y;
+  int32_t own_global_pml;
+} hd_decomp;
+
+typedef struct hd_ctx hd_ctx;
+
+/* Creates a context for one medium (Sec. 2, Eq. (pml)): copies the grid and
+ * decomposition, computes k^2 = (omega / c)^2 on the device from the velocity
+ * c_dev (FP64, NY x NX, device memory, read during the call only), the global
+ * and per-box PML stretching tables and the box tables.  Allocates its own
+ * device tables (about 8 NX NY bytes plus O(boxes) ); synchronises `stream`
+ * before returning.  On error *out is NULL. */
+int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *decomp, const double *c_dev,
+                    int32_t precision, void *stream);
+
+/* Bytes the caller must provide:
+ *   factor_bytes  : the per-box Schur inverses written by hd_factor_subdomains
+ *   krylov_bytes  : FGMRES bases V (restart+1 vectors) and Z (restart vectors),
+ *                   two work vectors and the Hessenberg/reduction scratch, for
+ *                   nrhs right-hand sides
+ *   scratch_bytes : per-box staging of the local substitutions (apply) and the
+ *                   per-box working matrix (factorisation)
+ * Any output pointer may be NULL. */
+int hd_query_workspace(const hd_ctx *ctx, int32_t nrhs, int32_t restart, size_t *factor_bytes,
+                       size_t *krylov_bytes, size_t *scratch_bytes);
+
+/* Factorises every local PML problem of Eq. (pmlij) (Sec. 3: "factorized and
+ * solved with direct solver") as a block-tridiagonal LU along the grid rows of
+ * the box: S_0 = D_0, S_j = D_j - L_j S_{j-1}^{-1} U_{j-1} (L_j, U_j diagonal,
+ * D_j tridiagonal), storing every S_j^{-1} (m x m, m = box width, column-major)
+ * in factor_dev.  Each S_j is inverted by Gauss-Jordan elimination with
+ * partial pivoting.  factor_dev stays bound to the context (the caller keeps
+ * it alive until hd_destroy or the next factorisation).  scratch_dev is free
+ * again when the call's work on `stream` ends.  Returns HD_ERR_NUMERIC later
+ * (from hd_gmres_solve / hd_check_status) if a pivot was zero. */
+int hd_factor_subdomains(hd_ctx *ctx, void *factor_dev, size_t factor_bytes, void *scratch_dev,
+                         size_t scratch_bytes, void *stream);
+
+/* y = A x for nrhs vectors: A is the PML operator of Eq. (pml) multiplied by
+ * J h^2 (J = alpha1 alpha2), a complex-symmetric 5-point matrix with
+ * homogeneous Dirichlet values outside Omega.  x_dev, y_dev: complex128
+ * [nrhs][NY][NX], must not overlap. */
+int hd_matvec(hd_ctx *ctx, const void *x_dev, void *y_dev, int32_t nrhs, void *stream);
+
+/* b = J h^2 f: the right-hand side of the scaled system for source samples f
+ * (complex128 [nrhs][NY][NX]); b may equal f. */
+int hd_rhs_from_source(hd_ctx *ctx, const void *f_dev, void *b_dev, int32_t nrhs, void *stream);
+
+/* z = sum_ij E_ij^T A_ij^{-1} X_ij r, Eq. (ddm0) + Eq. (pc): X_ij restricts r to
+ * the owned box, A_ij is the local PML operator of Eq. (pmlij) on the
+ * overlapping box (solved with the stored factors), E_ij^T extends the local
+ * solution over the whole box, PML area included, and the sum runs in a fixed
+ * order (deterministic).  r_dev, z_dev: complex128 [nrhs][NY][NX], must not
+ * overlap.  Needs a prior hd_factor_subdomains.  scratch_dev: at least
+ * scratch_bytes of hd_query_workspace for nrhs = 1 (right-hand sides are
+ * processed one after another). */
+int hd_apply_precond(hd_ctx *ctx, const void *r_dev, void *z_dev, int32_t nrhs, void *scratch_dev,
+                     size_t scratch_bytes, void *stream);
+
+typedef struct {
+  int32_t restart;    /* Krylov vectors per cycle                                  */
+  int32_t max_iters;  /* Arnoldi steps over all cycles                             */
+  double rtol;        /* stop when ||b - A x|| <= rtol ||b||                        */
+  int32_t use_x0;     /* 1: start from x_dev, 0: x0 = 0                              */
+} hd_gmres_opts;
+
+typedef struct {
+  int32_t iters;        /* Arnoldi steps over all cycles                            */
+  int32_t restarts;     /* completed cycles                                          */
+  int32_t converged;    /* 1 if the true relative residual <= rtol                   */
+  int32_t status;       /* hd_status of this right-hand side                         */
+  double relres_est;    /* |g_{k}| / ||b|| from the Givens recurrence                */
+  double relres_true;   /* ||b - A x|| / ||b|| recomputed in FP64                    */
+  double t_solve_s;     /* wall time of the solve on the host                        */
+} hd_gmres_stats;
+
+/* Restarted right-preconditioned flexible GMRES (Sec. 3; Z_j = M v_j stored):
+ * classical Gram-Schmidt applied twice in FP64, complex Givens rotations with
+ * real cosine, x += Z y at the end of each cycle, and the FP64 true residual
+ * b - A x decides convergence.  Blocking: returns when every right-hand side
+ * has converged or failed, with stats_host[nrhs] filled in.  b_dev, x_dev:
+ * complex128 [nrhs][NY][NX]; x_dev is the output (and the start when use_x0).
+ * krylov_dev/scratch_dev sized by hd_query_workspace for (1, restart): the
+ * right-hand sides are solved one after another. */
+int hd_gmres_solve(hd_ctx *ctx, const void *b_dev, void *x_dev, int32_t nrhs, const hd_gmres_opts *opts,
+                   void *krylov_dev, size_t krylov_bytes, void *scratch_dev, size_t scratch_bytes,
+                   hd_gmres_stats *stats_host, void *stream);
+
+/* Per-kernel-class timing with CUDA events recorded on the launching stream
+ * (events only while profiling is on; off by default).  Classes: 0
+ * factorisation, 1 restrict + forward/back substitution, 2 gather-sum,
+ * 3 matvec/residual, 4 Arnoldi (dots, updates, Givens, solution update),
+ * 5 other.  hd_get_timers writes ms[class] (accumulated device time, profiled
+ * launches only) and launches[class] (kernels launched, always counted) for up
+ * to n classes and synchronises `stream`; reset = 1 clears both afterwards. */
+int hd_set_profiling(hd_ctx *ctx, int32_t on);
+int hd_get_timers(hd_ctx *ctx, double *ms, int64_t *launches, int32_t n, int32_t reset, void *stream);
+
+/* Reads the device status word (set by kernels on a zero pivot, a non-finite
+ * value or a bounded wait that gave up), synchronising `stream`; clear = 1
+ * resets it. */
+int hd_check_status(hd_ctx *ctx, int32_t clear, void *stream);
+
+/* Frees the context's own device tables (not the caller's workspaces). */
+int hd_destroy(hd_ctx *ctx);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char *hd_last_error(void);
+
+/* Library version string. */
+const char *hd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HD_H_ */

@@ -1,0 +1,180 @@
+"""ctypes binding of libhd.so: the C ABI entry points under the same names.
+
+Argument marshalling only: every step of the solver runs in the library's CUDA
+kernels.  Pointers are passed as integers (``tensor.data_ptr()``), streams as
+``torch.cuda.Stream.cuda_stream`` integers.  The library must have been built
+(``paper_1508_02897_gb300.build.build()``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhd.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "hd.h")
+
+HD_OK, HD_ERR_INVALID, HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_NOT_CONVERGED, HD_ERR_NUMERIC, HD_ERR_TIMEOUT, HD_PENDING = range(8)
+HD_C128, HD_C64 = 0, 1
+STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID", 2: "HD_ERR_OOM", 3: "HD_ERR_CUDA", 4: "HD_ERR_NOT_CONVERGED",
+                5: "HD_ERR_NUMERIC", 6: "HD_ERR_TIMEOUT", 7: "HD_PENDING"}
+TIMER_CLASSES = ("factor", "subst", "gather", "matvec", "arnoldi", "other")
+
+
+class hd_grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int32), ("ny", ct.c_int32), ("npml", ct.c_int32), ("h", ct.c_double),
+                ("omega", ct.c_double), ("sigma0_over_omega", ct.c_double), ("pml_power", ct.c_int32)]
+
+
+class hd_decomp(ct.Structure):
+    _fields_ = [("nbx", ct.c_int32), ("nby", ct.c_int32), ("overlap", ct.c_int32),
+                ("cut_x", ct.POINTER(ct.c_int32)), ("cut_y", ct.POINTER(ct.c_int32)),
+                ("own_global_pml", ct.c_int32)]
+
+
+class hd_gmres_opts(ct.Structure):
+    _fields_ = [("restart", ct.c_int32), ("max_iters", ct.c_int32), ("rtol", ct.c_double), ("use_x0", ct.c_int32)]
+
+
+class hd_gmres_stats(ct.Structure):
+    _fields_ = [("iters", ct.c_int32), ("restarts", ct.c_int32), ("converged", ct.c_int32), ("status", ct.c_int32),
+                ("relres_est", ct.c_double), ("relres_true", ct.c_double), ("t_solve_s", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class HDError(RuntimeError):
+    def __init__(self, fn, code, msg):
+        super().__init__(f"{fn} failed with {STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_P = ct.c_void_p
+_SIGS = {
+    "hd_setup_medium": [ct.POINTER(_P), ct.POINTER(hd_grid), ct.POINTER(hd_decomp), _P, ct.c_int32, _P],
+    "hd_query_workspace": [_P, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t),
+                           ct.POINTER(ct.c_size_t)],
+    "hd_factor_subdomains": [_P, _P, ct.c_size_t, _P, ct.c_size_t, _P],
+    "hd_matvec": [_P, _P, _P, ct.c_int32, _P],
+    "hd_rhs_from_source": [_P, _P, _P, ct.c_int32, _P],
+    "hd_apply_precond": [_P, _P, _P, ct.c_int32, _P, ct.c_size_t, _P],
+    "hd_gmres_solve": [_P, _P, _P, ct.c_int32, ct.POINTER(hd_gmres_opts), _P, ct.c_size_t, _P, ct.c_size_t,
+                       ct.POINTER(hd_gmres_stats), _P],
+    "hd_set_profiling": [_P, ct.c_int32],
+    "hd_get_timers": [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32, ct.c_int32, _P],
+    "hd_check_status": [_P, ct.c_int32, _P],
+    "hd_destroy": [_P],
+    "hd_last_error": [],
+    "hd_version": [],
+}
+
+_lib = None
+
+
+def declared_symbols():
+    """Names of the functions declared in include/hd.h."""
+    with open(HEADER) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(hd_\w+)\s*\(", text, flags=re.M)))
+
+
+def lib():
+    """Loads libhd.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libhd.so not found at {LIB_PATH}: run paper_1508_02897_gb300.build.build() first")
+        L = ct.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ct.c_char_p if name in ("hd_last_error", "hd_version") else ct.c_int
+        _lib = L
+    return _lib
+
+
+def _check(fn, rc, allow=()):
+    if rc != HD_OK and rc not in allow:
+        raise HDError(fn, rc, lib().hd_last_error().decode())
+    return rc
+
+
+def _cuts(cuts):
+    if cuts is None:
+        return None, None
+    arr = (ct.c_int32 * len(cuts))(*[int(c) for c in cuts])
+    return arr, ct.cast(arr, ct.POINTER(ct.c_int32))
+
+
+def hd_setup_medium(nx, ny, npml, h, omega, c_ptr, precision, stream, nbx, nby, overlap, cut_x=None, cut_y=None,
+                    own_global_pml=1, sigma0_over_omega=20.0, pml_power=2):
+    g = hd_grid(nx, ny, npml, h, omega, sigma0_over_omega, pml_power)
+    kx, px = _cuts(cut_x)
+    ky, py = _cuts(cut_y)
+    d = hd_decomp(nbx, nby, overlap, px, py, own_global_pml)
+    ctx = _P()
+    _check("hd_setup_medium", lib().hd_setup_medium(ct.byref(ctx), ct.byref(g), ct.byref(d), c_ptr, precision, stream))
+    return ctx
+
+
+def hd_query_workspace(ctx, nrhs, restart):
+    f, k, s = ct.c_size_t(), ct.c_size_t(), ct.c_size_t()
+    _check("hd_query_workspace", lib().hd_query_workspace(ctx, nrhs, restart, ct.byref(f), ct.byref(k), ct.byref(s)))
+    return f.value, k.value, s.value
+
+
+def hd_factor_subdomains(ctx, factor_ptr, factor_bytes, scratch_ptr, scratch_bytes, stream):
+    _check("hd_factor_subdomains", lib().hd_factor_subdomains(ctx, factor_ptr, factor_bytes, scratch_ptr, scratch_bytes, stream))
+
+
+def hd_matvec(ctx, x_ptr, y_ptr, nrhs, stream):
+    _check("hd_matvec", lib().hd_matvec(ctx, x_ptr, y_ptr, nrhs, stream))
+
+
+def hd_rhs_from_source(ctx, f_ptr, b_ptr, nrhs, stream):
+    _check("hd_rhs_from_source", lib().hd_rhs_from_source(ctx, f_ptr, b_ptr, nrhs, stream))
+
+
+def hd_apply_precond(ctx, r_ptr, z_ptr, nrhs, scratch_ptr, scratch_bytes, stream):
+    _check("hd_apply_precond", lib().hd_apply_precond(ctx, r_ptr, z_ptr, nrhs, scratch_ptr, scratch_bytes, stream))
+
+
+def hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, restart, max_iters, rtol, krylov_ptr, krylov_bytes, scratch_ptr,
+                   scratch_bytes, stream, use_x0=0, raise_on_not_converged=False):
+    o = hd_gmres_opts(restart, max_iters, rtol, use_x0)
+    st = (hd_gmres_stats * nrhs)()
+    allow = () if raise_on_not_converged else (HD_ERR_NOT_CONVERGED,)
+    rc = _check("hd_gmres_solve", lib().hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, ct.byref(o), krylov_ptr, krylov_bytes,
+                                                       scratch_ptr, scratch_bytes, st, stream), allow)
+    return rc, [s.as_dict() for s in st]
+
+
+def hd_set_profiling(ctx, on):
+    _check("hd_set_profiling", lib().hd_set_profiling(ctx, int(bool(on))))
+
+
+def hd_get_timers(ctx, stream, reset=False):
+    n = len(TIMER_CLASSES)
+    ms = (ct.c_double * n)()
+    la = (ct.c_int64 * n)()
+    _check("hd_get_timers", lib().hd_get_timers(ctx, ms, la, n, int(reset), stream))
+    return {TIMER_CLASSES[i]: (ms[i], la[i]) for i in range(n)}
+
+
+def hd_check_status(ctx, stream, clear=True):
+    return _check("hd_check_status", lib().hd_check_status(ctx, int(clear), stream))
+
+
+def hd_destroy(ctx):
+    _check("hd_destroy", lib().hd_destroy(ctx))
+
+
+def hd_last_error():
+    return lib().hd_last_error().decode()
+
+
+def hd_version():
+    return lib().hd_version().decode()

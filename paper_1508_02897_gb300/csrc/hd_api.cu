@@ -1,0 +1,381 @@
+// C ABI of libhd: argument checks, context set-up (decomposition tables of
+// Sec. 2), workspace sizing, error reporting and kernel timing.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hd_internal.cuh"
+
+namespace hd {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char *what) {
+  set_error(std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e));
+  return HD_ERR_CUDA;
+}
+
+static int invalid(const std::string &msg) {
+  set_error(msg);
+  return HD_ERR_INVALID;
+}
+
+// ---------------------------------------------------------------- timers
+static cudaEvent_t get_event(hd_ctx *ctx) {
+  if (ctx->ev_next < ctx->ev_pool.size()) return ctx->ev_pool[ctx->ev_next++];
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  ctx->ev_pool.push_back(e);
+  ctx->ev_next = ctx->ev_pool.size();
+  return e;
+}
+
+void tic(hd_ctx *ctx, int cls, cudaStream_t st) {
+  if (!ctx->profiling) return;
+  cudaEvent_t a = get_event(ctx);
+  if (!a) return;
+  cudaEventRecord(a, st);
+  ctx->ev_pending.push_back({cls, {a, nullptr}});
+}
+
+void toc(hd_ctx *ctx, int cls, cudaStream_t st, int nkernels) {
+  ctx->t_launch[cls] += nkernels;
+  if (!ctx->profiling || ctx->ev_pending.empty()) return;
+  auto &p = ctx->ev_pending.back();
+  if (p.first != cls || p.second.second) return;
+  cudaEvent_t b = get_event(ctx);
+  if (!b) return;
+  cudaEventRecord(b, st);
+  p.second.second = b;
+}
+
+int collect_timers(hd_ctx *ctx) {
+  for (auto &p : ctx->ev_pending) {
+    if (!p.second.second) continue;
+    cudaEventSynchronize(p.second.second);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.second.first, p.second.second) == cudaSuccess) {
+      ctx->t_ms[p.first] += ms;
+    }
+  }
+  ctx->ev_pending.clear();
+  ctx->ev_next = 0;
+  return HD_OK;
+}
+
+size_t krylov_bytes(int64_t n, int restart);
+int run_gmres_one(hd_ctx *ctx, const double2 *b, double2 *x, const hd_gmres_opts *o, void *kws, void *scratch,
+                  hd_gmres_stats *stats, double *host_stat, cudaStream_t st);
+
+static void free_ctx(hd_ctx *c) {
+  if (!c) return;
+  cudaFree(c->d_k2);
+  cudaFree(c->d_gax_c);
+  cudaFree(c->d_giax_f);
+  cudaFree(c->d_gay_c);
+  cudaFree(c->d_giay_f);
+  cudaFree(c->d_lpool);
+  cudaFree(c->d_subs);
+  cudaFree(c->d_axx);
+  cudaFree(c->d_axy);
+  cudaFree(c->d_nearx);
+  cudaFree(c->d_neary);
+  cudaFree(c->d_status);
+  if (c->host_stat) cudaFreeHost(c->host_stat);
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  delete c;
+}
+
+// Owned ranges and extents along one axis (Sec. 2: x_{i,0}, x_{i,1}).
+static int axis_ranges(int n_in, int npml, int nb, int overlap, const int32_t *cut, int own_global_pml,
+                       std::vector<AxisDev> &out, std::vector<int32_t> &near, const char *name) {
+  const int n = n_in + 2 * npml;
+  std::vector<int32_t> c(nb + 1);
+  for (int i = 0; i <= nb; ++i) c[i] = cut ? cut[i] : npml + (int32_t)(((int64_t)i * n_in) / nb);
+  if (c[0] != npml || c[nb] != npml + n_in)
+    return invalid(std::string(name) + ": cut points must start at npml and end at npml + n");
+  for (int i = 0; i < nb; ++i) {
+    if (c[i + 1] <= c[i]) return invalid(std::string(name) + ": cut points must increase");
+    if (nb > 1 && c[i + 1] - c[i] < overlap + npml)
+      return invalid(std::string(name) + ": every owned width must be at least overlap + npml");
+  }
+  out.resize(nb);
+  near.assign(n, 0);
+  for (int i = 0; i < nb; ++i) {
+    AxisDev a;
+    a.o0 = c[i];
+    a.o1 = c[i + 1];
+    a.e0 = c[i] - npml - (i > 0 ? overlap : 0);
+    a.e1 = c[i + 1] + npml + (i < nb - 1 ? overlap : 0);
+    if (a.e0 < 0 || a.e1 > n) return invalid(std::string(name) + ": an overlapping box leaves the domain");
+    if (own_global_pml) {
+      if (i == 0) a.o0 = 0;
+      if (i == nb - 1) a.o1 = n;
+    }
+    out[i] = a;
+    int lo = i == 0 ? 0 : c[i], hi = i == nb - 1 ? n : c[i + 1];
+    for (int g = lo; g < hi; ++g) near[g] = i;
+  }
+  return HD_OK;
+}
+
+constexpr int kMaxBoxWidth = 256;
+
+}  // namespace hd
+
+using namespace hd;
+
+extern "C" {
+
+const char *hd_last_error(void) { return g_err.c_str(); }
+
+const char *hd_version(void) { return "hd 0.1 (sm_103a)"; }
+
+int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, const double *c_dev, int32_t precision,
+                    void *stream) {
+  if (!out) return invalid("hd_setup_medium: out is NULL");
+  *out = nullptr;
+  if (!grid || !dec || !c_dev) return invalid("hd_setup_medium: NULL argument");
+  if (grid->nx < 1 || grid->ny < 1 || grid->npml < 0 || !(grid->h > 0) || !(grid->omega > 0) || grid->pml_power < 0 ||
+      grid->pml_power > 8 || !std::isfinite(grid->sigma0_over_omega))
+    return invalid("hd_setup_medium: bad grid");
+  if (dec->nbx < 1 || dec->nby < 1 || dec->overlap < 0 || dec->nbx > grid->nx || dec->nby > grid->ny)
+    return invalid("hd_setup_medium: bad decomposition");
+  if (precision != HD_C128 && precision != HD_C64) return invalid("hd_setup_medium: bad precision");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  hd_ctx *c = new (std::nothrow) hd_ctx();
+  if (!c) { set_error("hd_setup_medium: host allocation failed"); return HD_ERR_OOM; }
+  c->nx_in = grid->nx; c->ny_in = grid->ny; c->npml = grid->npml;
+  c->NX = grid->nx + 2 * grid->npml; c->NY = grid->ny + 2 * grid->npml;
+  c->h = grid->h; c->omega = grid->omega; c->s0 = grid->sigma0_over_omega; c->power = grid->pml_power;
+  c->prec = precision;
+  c->nbx = dec->nbx; c->nby = dec->nby; c->overlap = dec->overlap; c->own_global_pml = dec->own_global_pml ? 1 : 0;
+  std::vector<int32_t> nearx, neary;
+  int rc = axis_ranges(grid->nx, grid->npml, dec->nbx, dec->overlap, dec->cut_x, c->own_global_pml, c->axx, nearx, "x");
+  if (!rc) rc = axis_ranges(grid->ny, grid->npml, dec->nby, dec->overlap, dec->cut_y, c->own_global_pml, c->axy, neary, "y");
+  if (rc) { free_ctx(c); return rc; }
+  c->nsub = c->nbx * c->nby;
+  c->subs.resize(c->nsub);
+  int64_t foff = 0, soff = 0, woff = 0;
+  int32_t aoff = 0;
+  c->max_m = 0; c->max_rows = 0;
+  for (int iy = 0; iy < c->nby; ++iy)
+    for (int ix = 0; ix < c->nbx; ++ix) {
+      SubDev &s = c->subs[iy * c->nbx + ix];
+      const AxisDev &ax = c->axx[ix], &ay = c->axy[iy];
+      s.ex0 = ax.e0; s.ex = ax.e1 - ax.e0; s.ey0 = ay.e0; s.ey = ay.e1 - ay.e0;
+      s.ox0 = ax.o0; s.ox1 = ax.o1; s.oy0 = ay.o0; s.oy1 = ay.o1;
+      s.ix = ix; s.iy = iy;
+      s.foff = foff; foff += (int64_t)s.ey * s.ex * s.ex;
+      s.soff = soff; soff += (int64_t)s.ex * s.ey;
+      s.woff = woff; woff += (int64_t)s.ex * s.ex;
+      s.aoff = aoff; aoff += 2 * s.ex + 2 * s.ey + 2;
+      c->max_m = std::max(c->max_m, s.ex);
+      c->max_rows = std::max(c->max_rows, s.ey);
+    }
+  if (c->max_m > kMaxBoxWidth) {
+    free_ctx(c);
+    return invalid("hd_setup_medium: a box is wider than 256 cells (use more boxes along x)");
+  }
+  c->factor_elems = foff; c->staging_elems = soff; c->work_elems = woff;
+  const int64_t n = (int64_t)c->NX * c->NY;
+#define ALLOC(p, bytes)                                                     \
+  do {                                                                      \
+    cudaError_t e_ = cudaMalloc(&(p), (bytes));                             \
+    if (e_ != cudaSuccess) { free_ctx(c); return cuda_fail(e_, "cudaMalloc"); } \
+  } while (0)
+  ALLOC(c->d_k2, sizeof(double) * n);
+  ALLOC(c->d_gax_c, sizeof(double2) * c->NX);
+  ALLOC(c->d_giax_f, sizeof(double2) * (c->NX + 1));
+  ALLOC(c->d_gay_c, sizeof(double2) * c->NY);
+  ALLOC(c->d_giay_f, sizeof(double2) * (c->NY + 1));
+  ALLOC(c->d_lpool, sizeof(double2) * aoff);
+  ALLOC(c->d_subs, sizeof(SubDev) * c->nsub);
+  ALLOC(c->d_axx, sizeof(AxisDev) * c->nbx);
+  ALLOC(c->d_axy, sizeof(AxisDev) * c->nby);
+  ALLOC(c->d_nearx, sizeof(int32_t) * c->NX);
+  ALLOC(c->d_neary, sizeof(int32_t) * c->NY);
+  ALLOC(c->d_status, sizeof(int32_t));
+#undef ALLOC
+  cudaError_t e = cudaMallocHost(&c->host_stat, 8 * sizeof(double));
+  if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "cudaMallocHost"); }
+#define CP(dst, src, bytes)                                                                        \
+  do {                                                                                             \
+    cudaError_t e_ = cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyHostToDevice, st);           \
+    if (e_ != cudaSuccess) { free_ctx(c); return cuda_fail(e_, "cudaMemcpyAsync"); }               \
+  } while (0)
+  CP(c->d_subs, c->subs.data(), sizeof(SubDev) * c->nsub);
+  CP(c->d_axx, c->axx.data(), sizeof(AxisDev) * c->nbx);
+  CP(c->d_axy, c->axy.data(), sizeof(AxisDev) * c->nby);
+  CP(c->d_nearx, nearx.data(), sizeof(int32_t) * c->NX);
+  CP(c->d_neary, neary.data(), sizeof(int32_t) * c->NY);
+#undef CP
+  e = cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = launch_setup_tables(c, c_dev, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "hd_setup_medium"); }
+  int32_t status = 0;
+  e = cudaMemcpy(&status, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "hd_setup_medium status"); }
+  if (status) { free_ctx(c); set_error("hd_setup_medium: velocity must be finite and positive"); return HD_ERR_NUMERIC; }
+  c->t_launch[T_OTHER] += 3;  // the three table kernels above
+  *out = c;
+  return HD_OK;
+}
+
+int hd_query_workspace(const hd_ctx *c, int32_t nrhs, int32_t restart, size_t *factor_bytes, size_t *krylov_bytes_out,
+                       size_t *scratch_bytes) {
+  if (!c) return invalid("hd_query_workspace: NULL context");
+  if (nrhs < 1 || restart < 1) return invalid("hd_query_workspace: nrhs and restart must be >= 1");
+  size_t cs = c->prec == HD_C64 ? sizeof(float2) : sizeof(double2);
+  if (factor_bytes) *factor_bytes = cs * (size_t)c->factor_elems;
+  if (scratch_bytes) *scratch_bytes = cs * (size_t)std::max(c->staging_elems, c->work_elems);
+  if (krylov_bytes_out) *krylov_bytes_out = krylov_bytes((int64_t)c->NX * c->NY, restart);
+  return HD_OK;
+}
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int hd_factor_subdomains(hd_ctx *c, void *factor, size_t factor_bytes, void *scratch, size_t scratch_bytes,
+                         void *stream) {
+  if (!c || !factor || !scratch) return invalid("hd_factor_subdomains: NULL argument");
+  size_t fb, sb;
+  hd_query_workspace(c, 1, 1, &fb, nullptr, &sb);
+  if (factor_bytes < fb) { set_error("hd_factor_subdomains: factor workspace too small"); return HD_ERR_OOM; }
+  if (scratch_bytes < sb) { set_error("hd_factor_subdomains: scratch workspace too small"); return HD_ERR_OOM; }
+  if (!aligned16(factor) || !aligned16(scratch)) return invalid("hd_factor_subdomains: buffers must be 16-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int rc = run_factor(c, factor, scratch, st);
+  if (rc) return rc;
+  c->factor = factor;
+  c->factored = true;
+  return HD_OK;
+}
+
+int hd_matvec(hd_ctx *c, const void *x, void *y, int32_t nrhs, void *stream) {
+  if (!c || !x || !y || nrhs < 1) return invalid("hd_matvec: bad argument");
+  if (!aligned16(x) || !aligned16(y)) return invalid("hd_matvec: vectors must be 16-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = (int64_t)c->NX * c->NY;
+  for (int r = 0; r < nrhs; ++r) {
+    tic(c, T_MATVEC, st);
+    cudaError_t e = launch_matvec(c, reinterpret_cast<const double2 *>(x) + r * n, reinterpret_cast<double2 *>(y) + r * n, st);
+    toc(c, T_MATVEC, st, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "hd_matvec");
+  }
+  return HD_OK;
+}
+
+int hd_rhs_from_source(hd_ctx *c, const void *f, void *b, int32_t nrhs, void *stream) {
+  if (!c || !f || !b || nrhs < 1) return invalid("hd_rhs_from_source: bad argument");
+  if (!aligned16(f) || !aligned16(b)) return invalid("hd_rhs_from_source: vectors must be 16-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = (int64_t)c->NX * c->NY;
+  for (int r = 0; r < nrhs; ++r) {
+    cudaError_t e = launch_rhs(c, reinterpret_cast<const double2 *>(f) + r * n, reinterpret_cast<double2 *>(b) + r * n, st);
+    c->t_launch[T_OTHER] += 1;
+    if (e != cudaSuccess) return cuda_fail(e, "hd_rhs_from_source");
+  }
+  return HD_OK;
+}
+
+int hd_apply_precond(hd_ctx *c, const void *r, void *z, int32_t nrhs, void *scratch, size_t scratch_bytes,
+                     void *stream) {
+  if (!c || !r || !z || !scratch || nrhs < 1) return invalid("hd_apply_precond: bad argument");
+  if (!c->factored) return invalid("hd_apply_precond: call hd_factor_subdomains first");
+  size_t sb;
+  hd_query_workspace(c, 1, 1, nullptr, nullptr, &sb);
+  if (scratch_bytes < sb) { set_error("hd_apply_precond: scratch workspace too small"); return HD_ERR_OOM; }
+  if (!aligned16(r) || !aligned16(z) || !aligned16(scratch)) return invalid("hd_apply_precond: buffers must be 16-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = (int64_t)c->NX * c->NY;
+  for (int k = 0; k < nrhs; ++k) {
+    int rc = run_apply(c, reinterpret_cast<const double2 *>(r) + k * n, reinterpret_cast<double2 *>(z) + k * n, scratch, st);
+    if (rc) return rc;
+  }
+  return HD_OK;
+}
+
+int hd_gmres_solve(hd_ctx *c, const void *b, void *x, int32_t nrhs, const hd_gmres_opts *o, void *kws, size_t kbytes,
+                   void *scratch, size_t scratch_bytes, hd_gmres_stats *stats, void *stream) {
+  if (!c || !b || !x || !o || !kws || !scratch || !stats || nrhs < 1) return invalid("hd_gmres_solve: bad argument");
+  if (!c->factored) return invalid("hd_gmres_solve: call hd_factor_subdomains first");
+  if (o->restart < 1 || o->max_iters < 0 || !(o->rtol >= 0)) return invalid("hd_gmres_solve: bad options");
+  size_t kb, sb;
+  hd_query_workspace(c, 1, o->restart, nullptr, &kb, &sb);
+  if (kbytes < kb) { set_error("hd_gmres_solve: krylov workspace too small"); return HD_ERR_OOM; }
+  if (scratch_bytes < sb) { set_error("hd_gmres_solve: scratch workspace too small"); return HD_ERR_OOM; }
+  if (!aligned16(b) || !aligned16(x) || !aligned16(kws) || !aligned16(scratch))
+    return invalid("hd_gmres_solve: buffers must be 16-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int64_t n = (int64_t)c->NX * c->NY;
+  int worst = HD_OK;
+  for (int k = 0; k < nrhs; ++k) {
+    std::memset(&stats[k], 0, sizeof(hd_gmres_stats));
+    int rc = run_gmres_one(c, reinterpret_cast<const double2 *>(b) + k * n, reinterpret_cast<double2 *>(x) + k * n, o,
+                           kws, scratch, &stats[k], c->host_stat, st);
+    stats[k].status = rc;
+    if (rc == HD_ERR_CUDA) return rc;
+    if (rc && !worst) worst = rc;
+  }
+  int32_t status = 0;
+  cudaError_t e = cudaMemcpyAsync(c->host_stat, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "hd_gmres_solve status");
+  std::memcpy(&status, c->host_stat, sizeof(int32_t));
+  if (status) { set_error("hd_gmres_solve: a zero pivot or non-finite value was flagged on the device"); return HD_ERR_NUMERIC; }
+  if (worst == HD_ERR_NOT_CONVERGED) set_error("hd_gmres_solve: not converged within max_iters");
+  return worst;
+}
+
+int hd_set_profiling(hd_ctx *c, int32_t on) {
+  if (!c) return invalid("hd_set_profiling: NULL context");
+  c->profiling = on != 0;
+  return HD_OK;
+}
+
+int hd_get_timers(hd_ctx *c, double *ms, int64_t *launches, int32_t n, int32_t reset, void *stream) {
+  if (!c) return invalid("hd_get_timers: NULL context");
+  cudaError_t e = cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "hd_get_timers");
+  collect_timers(c);
+  for (int i = 0; i < n && i < T_NCLASS; ++i) {
+    if (ms) ms[i] = c->t_ms[i];
+    if (launches) launches[i] = c->t_launch[i];
+  }
+  if (reset)
+    for (int i = 0; i < T_NCLASS; ++i) { c->t_ms[i] = 0; c->t_launch[i] = 0; }
+  return HD_OK;
+}
+
+int hd_check_status(hd_ctx *c, int32_t clear, void *stream) {
+  if (!c) return invalid("hd_check_status: NULL context");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(c->host_stat, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "hd_check_status");
+  int32_t status;
+  std::memcpy(&status, c->host_stat, sizeof(int32_t));
+  if (clear) {
+    e = cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return cuda_fail(e, "hd_check_status clear");
+  }
+  if (status & ST_TIMEOUT) { set_error("device wait gave up"); return HD_ERR_TIMEOUT; }
+  if (status) { set_error("zero pivot or non-finite value flagged on the device"); return HD_ERR_NUMERIC; }
+  return HD_OK;
+}
+
+int hd_destroy(hd_ctx *c) {
+  if (!c) return HD_OK;
+  cudaDeviceSynchronize();
+  free_ctx(c);
+  return HD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+// Internal declarations shared by the translation units of libhd.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/hd.h"
+
+namespace hd {
+
+// ---------------------------------------------------------------- complex helpers
+template <typename R> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename R> using C = typename cplx<R>::type;
+
+template <typename T> __host__ __device__ __forceinline__ T mk(decltype(T::x) re, decltype(T::x) im) {
+  T z; z.x = re; z.y = im; return z;
+}
+template <typename T> __host__ __device__ __forceinline__ T cadd(T a, T b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __host__ __device__ __forceinline__ T csub(T a, T b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __host__ __device__ __forceinline__ T cmul(T a, T b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc + a*b
+template <typename T> __host__ __device__ __forceinline__ T cfma(T a, T b, T acc) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc - a*b
+template <typename T> __host__ __device__ __forceinline__ T cfms(T a, T b, T acc) {
+  acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(-a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+// acc + conj(a)*b
+template <typename T> __host__ __device__ __forceinline__ T cfma_conj(T a, T b, T acc) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+template <typename T> __host__ __device__ __forceinline__ T cinv(T a) {
+  auto d = a.x * a.x + a.y * a.y;
+  return mk<T>(a.x / d, -a.y / d);
+}
+__host__ __device__ __forceinline__ float2 to_c(double2 z, float2) { return make_float2((float)z.x, (float)z.y); }
+__host__ __device__ __forceinline__ double2 to_c(double2 z, double2) { return z; }
+__host__ __device__ __forceinline__ double2 to_d(float2 z) { return make_double2(z.x, z.y); }
+__host__ __device__ __forceinline__ double2 to_d(double2 z) { return z; }
+
+// ---------------------------------------------------------------- tables
+// One overlapping box Omega_ij (global cell indices) and its owned box.
+struct SubDev {
+  int32_t ex0, ey0, ex, ey;      // extent origin and size
+  int32_t ox0, ox1, oy0, oy1;    // owned box [ox0, ox1) x [oy0, oy1)
+  int64_t foff;                  // offset of the factors (complex entries)
+  int64_t soff;                  // offset of the staging vector (complex entries)
+  int64_t woff;                  // offset of the factorisation working matrix (complex entries)
+  int32_t aoff;                  // offset into the local PML table pool
+  int32_t ix, iy;
+};
+
+// One axis of the decomposition: per box column (or row) its extent and owned range.
+struct AxisDev {
+  int32_t e0, e1, o0, o1;
+};
+
+enum TimerClass { T_FACTOR = 0, T_SUBST = 1, T_GATHER = 2, T_MATVEC = 3, T_ARNOLDI = 4, T_OTHER = 5, T_NCLASS = 6 };
+
+// Bits of the device status word.
+enum StatusBits { ST_ZERO_PIVOT = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
+
+}  // namespace hd
+
+struct hd_ctx {
+  // grid
+  int nx_in, ny_in, npml, NX, NY;
+  double h, omega, s0;
+  int power;
+  int prec;
+  // decomposition
+  int nbx, nby, overlap, own_global_pml;
+  int nsub;
+  std::vector<hd::SubDev> subs;
+  std::vector<hd::AxisDev> axx, axy;
+  int max_m, max_rows;
+  int64_t factor_elems, staging_elems, work_elems;
+  // device tables (owned)
+  double *d_k2 = nullptr;
+  double2 *d_gax_c = nullptr, *d_giax_f = nullptr, *d_gay_c = nullptr, *d_giay_f = nullptr;
+  double2 *d_lpool = nullptr;   // per-box PML tables: a1c[ex], ia1f[ex+1], a2c[ey], ia2f[ey+1]
+  hd::SubDev *d_subs = nullptr;
+  hd::AxisDev *d_axx = nullptr, *d_axy = nullptr;
+  int32_t *d_nearx = nullptr, *d_neary = nullptr;  // per global index: box column/row nearest
+  int32_t *d_status = nullptr;                    // device status word
+  double *host_stat = nullptr;                    // pinned host mirror of small device results
+  // factor binding
+  void *factor = nullptr;
+  bool factored = false;
+  // profiling
+  bool profiling = false;
+  double t_ms[hd::T_NCLASS] = {0};
+  int64_t t_launch[hd::T_NCLASS] = {0};
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  size_t ev_next = 0;
+};
+
+namespace hd {
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+#define HD_CUDA(call)                                         \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return ::hd::cuda_fail(e_, #call); \
+  } while (0)
+
+// profiling brackets around a launch on `st`
+void tic(hd_ctx *ctx, int cls, cudaStream_t st);
+void toc(hd_ctx *ctx, int cls, cudaStream_t st, int nkernels);
+int collect_timers(hd_ctx *ctx);
+
+// kernels launchers (return cudaError_t of the launch)
+cudaError_t launch_setup_tables(hd_ctx *ctx, const double *c_dev, cudaStream_t st);
+cudaError_t launch_matvec(hd_ctx *ctx, const double2 *x, double2 *y, cudaStream_t st);
+cudaError_t launch_residual(hd_ctx *ctx, const double2 *b, const double2 *x, double2 *r, cudaStream_t st);
+cudaError_t launch_rhs(hd_ctx *ctx, const double2 *f, double2 *b, cudaStream_t st);
+int run_factor(hd_ctx *ctx, void *factor, void *work, cudaStream_t st);
+int run_apply(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st);
+size_t factor_smem_bytes(int prec, int max_m);
+}  // namespace hd

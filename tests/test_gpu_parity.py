@@ -1,0 +1,149 @@
+"""CUDA path (through the C ABI) against the FP64 CPU oracle, element by element.
+
+Tolerances: the c128 path follows the same arithmetic in FP64 with a different
+direct solver (block Schur inverses vs. sparse LU), so results agree to
+rounding times the local condition number: matvec 1e-13, preconditioner 1e-10
+relative L2, FGMRES iterate after a fixed number of steps 1e-9.  The c64 path
+stores the local factors in complex FP32: preconditioner 2e-4 relative L2
+(FP32 rounding amplified by the local problems' condition number), final
+solution 1e-5 against the FP64 oracle at relative residual 1e-8.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import workloads as W
+from oracle import DDMPreconditioner, Grid, fgmres, global_operator, rhs_from_source
+from tests._cases import CASES, cuts, omega, velocity
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1508_02897_gb300.build import build  # noqa: E402
+
+build()
+from paper_1508_02897_gb300.solver import HelmholtzDDM  # noqa: E402
+
+
+def rel(a, b):
+    a = np.asarray(a).ravel(); b = np.asarray(b).ravel()
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+_oracles = {}
+
+
+def oracle(name, own=True):
+    key = (name, own)
+    if key not in _oracles:
+        case = CASES[name]
+        c = velocity(case)
+        g = Grid(case["N"], case["npml"], omega(case, c))
+        A = global_operator(g, c)
+        P = DDMPreconditioner(g, c, cuts(case), cuts(case), case["overlap"], own_global_pml=own)
+        _oracles[key] = (case, c, g, A, P)
+    return _oracles[key]
+
+
+def gpu(name, precision, own=True):
+    case, c, g, _, _ = oracle(name, own)
+    return HelmholtzDDM(case["N"], case["npml"], g.omega, c, case["nb"], case["nb"], case["overlap"],
+                        precision=precision, cut_x=cuts(case), cut_y=cuts(case), own_global_pml=own)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_matvec_and_rhs(name):
+    case, c, g, A, _ = oracle(name)
+    s = gpu(name, "c128")
+    x = W.random_complex((2, g.n, g.n), seed=7)
+    y = s.matvec(torch.from_numpy(x)).cpu().numpy()
+    for k in range(2):
+        ref = (A @ x[k].ravel()).reshape(g.n, g.n)
+        assert rel(y[k], ref) < 1e-13
+    f = W.gaussian_source(case["N"], case["npml"], 0.3, 0.6, 2.0 / case["N"])
+    b = s.rhs(torch.from_numpy(f)).cpu().numpy()
+    assert rel(b, rhs_from_source(g, f)) < 1e-14
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
+def test_precond_parity(name, precision, tol):
+    _, _, g, _, P = oracle(name)
+    s = gpu(name, precision)
+    r = W.random_complex((g.n, g.n), seed=3)
+    z = s.apply_precond(torch.from_numpy(r)).cpu().numpy()
+    ref = P.apply(r)
+    assert rel(z, ref) < tol
+    # deterministic: a second application is bitwise identical
+    z2 = s.apply_precond(torch.from_numpy(r)).cpu().numpy()
+    assert np.array_equal(z, z2)
+
+
+def test_precond_literal_ownership():
+    """Owned boxes on the interior only (the literal reading of Sec. 2)."""
+    _, _, g, _, P = oracle("ragged", own=False)
+    s = gpu("ragged", "c128", own=False)
+    r = W.random_complex((g.n, g.n), seed=8)
+    assert rel(s.apply_precond(torch.from_numpy(r)).cpu().numpy(), P.apply(r)) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged"])
+def test_gmres_fixed_steps_c128(name):
+    """Same FGMRES variant on both sides: the iterate after k steps agrees."""
+    case, c, g, A, P = oracle(name)
+    s = gpu(name, "c128")
+    f = W.gaussian_source(case["N"], case["npml"], 0.45, 0.55, 2.0 / case["N"])
+    b = rhs_from_source(g, f)
+    k = 4
+    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=3, rtol=1e-15, max_iters=k)
+    x, st = s.solve(torch.from_numpy(b), restart=3, rtol=1e-15, max_iters=k)
+    assert st[0]["iters"] == ref.iters == k
+    assert rel(x.cpu().numpy(), ref.x.reshape(g.n, g.n)) < 1e-9
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_gmres_converged_c128(name):
+    case, c, g, A, P = oracle(name)
+    s = gpu(name, "c128")
+    f = W.gaussian_source(case["N"], case["npml"], 0.5, 0.5, 2.0 / case["N"])
+    b = rhs_from_source(g, f)
+    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=50, rtol=1e-8, max_iters=300)
+    x, st = s.solve(torch.from_numpy(b), restart=50, rtol=1e-8, max_iters=300)
+    assert st[0]["converged"] == 1 and abs(st[0]["iters"] - ref.iters) <= 1
+    xn = x.cpu().numpy().ravel()
+    assert np.linalg.norm(b.ravel() - A @ xn) / np.linalg.norm(b) <= 1e-8
+    assert rel(xn, ref.x) < 1e-9
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_gmres_mixed_precision(name):
+    """c64 local factors, FP64 outer loop: FP64 relative residual reaches the
+    tolerance and the solution matches the FP64 oracle to 1e-5."""
+    case, c, g, A, P = oracle(name)
+    s = gpu(name, "c64")
+    f = W.gaussian_source(case["N"], case["npml"], 0.5, 0.5, 2.0 / case["N"])
+    b = rhs_from_source(g, f)
+    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=50, rtol=1e-10, max_iters=400)
+    x, st = s.solve(torch.from_numpy(b), restart=50, rtol=1e-8, max_iters=400)
+    xn = x.cpu().numpy().ravel()
+    assert st[0]["converged"] == 1
+    assert np.linalg.norm(b.ravel() - A @ xn) / np.linalg.norm(b) <= 1e-8
+    assert rel(xn, ref.x) < 1e-5
+
+
+def test_one_box_is_exact():
+    """Nb = 1: the preconditioner is the exact PML solve, so one iteration."""
+    N, npml = 96, 16
+    c = W.velocity_random_field(N, npml, seed=4)
+    om = 2 * np.pi * float(c.min()) * N / 10
+    g = Grid(N, npml, om)
+    A = global_operator(g, c)
+    s = HelmholtzDDM(N, npml, om, c, 1, 1, 8, precision="c128")
+    b = rhs_from_source(g, W.gaussian_source(N, npml, 0.4, 0.5, 2.0 / N))
+    x, st = s.solve(torch.from_numpy(b), restart=10, rtol=1e-10, max_iters=20)
+    assert st[0]["iters"] == 1 and st[0]["converged"] == 1
+    xn = x.cpu().numpy().ravel()
+    assert np.linalg.norm(b.ravel() - A @ xn) / np.linalg.norm(b) < 1e-11
