@@ -134,11 +134,20 @@ int hd_rhs_from_source(hd_ctx *ctx, const void *f_dev, void *b_dev, int32_t nrhs
 int hd_apply_precond(hd_ctx *ctx, const void *r_dev, void *z_dev, int32_t nrhs, void *scratch_dev,
                      size_t scratch_bytes, void *stream);
 
+/* Arithmetic of the Gram-Schmidt dot products and updates. */
+typedef enum {
+  HD_ARNOLDI_FP64 = 0,  /* IEEE FP64 throughout                                       */
+  HD_ARNOLDI_DS = 1     /* basis stored as float pairs (hi + lo, ~48-bit mantissa) and
+                           double-single arithmetic on the FP32 pipes; norms, Givens,
+                           least squares and the true residual stay FP64               */
+} hd_arnoldi_mode;
+
 typedef struct {
   int32_t restart;    /* Krylov vectors per cycle                                  */
   int32_t max_iters;  /* Arnoldi steps over all cycles                             */
   double rtol;        /* stop when ||b - A x|| <= rtol ||b||                        */
   int32_t use_x0;     /* 1: start from x_dev, 0: x0 = 0                              */
+  int32_t arnoldi;    /* hd_arnoldi_mode                                            */
 } hd_gmres_opts;
 
 typedef struct {
@@ -152,7 +161,8 @@ typedef struct {
 } hd_gmres_stats;
 
 /* Restarted right-preconditioned flexible GMRES (Sec. 3; Z_j = M v_j stored):
- * classical Gram-Schmidt applied twice in FP64, complex Givens rotations with
+ * classical Gram-Schmidt applied twice (FP64 or double-single, opts->arnoldi),
+ * FP64 norms and complex Givens rotations with
  * real cosine, x += Z y at the end of each cycle, and the FP64 true residual
  * b - A x decides convergence.  Blocking: returns when every right-hand side
  * has converged or failed, with stats_host[nrhs] filled in.  b_dev, x_dev:

@@ -17,6 +17,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "hd.h")
 
 HD_OK, HD_ERR_INVALID, HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_NOT_CONVERGED, HD_ERR_NUMERIC, HD_ERR_TIMEOUT, HD_PENDING = range(8)
 HD_C128, HD_C64 = 0, 1
+HD_ARNOLDI_FP64, HD_ARNOLDI_DS = 0, 1
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID", 2: "HD_ERR_OOM", 3: "HD_ERR_CUDA", 4: "HD_ERR_NOT_CONVERGED",
                 5: "HD_ERR_NUMERIC", 6: "HD_ERR_TIMEOUT", 7: "HD_PENDING"}
 TIMER_CLASSES = ("factor", "subst", "gather", "matvec", "arnoldi", "other")
@@ -34,7 +35,8 @@ class hd_decomp(ct.Structure):
 
 
 class hd_gmres_opts(ct.Structure):
-    _fields_ = [("restart", ct.c_int32), ("max_iters", ct.c_int32), ("rtol", ct.c_double), ("use_x0", ct.c_int32)]
+    _fields_ = [("restart", ct.c_int32), ("max_iters", ct.c_int32), ("rtol", ct.c_double), ("use_x0", ct.c_int32),
+                ("arnoldi", ct.c_int32)]
 
 
 class hd_gmres_stats(ct.Structure):
@@ -143,8 +145,8 @@ def hd_apply_precond(ctx, r_ptr, z_ptr, nrhs, scratch_ptr, scratch_bytes, stream
 
 
 def hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, restart, max_iters, rtol, krylov_ptr, krylov_bytes, scratch_ptr,
-                   scratch_bytes, stream, use_x0=0, raise_on_not_converged=False):
-    o = hd_gmres_opts(restart, max_iters, rtol, use_x0)
+                   scratch_bytes, stream, use_x0=0, arnoldi=HD_ARNOLDI_FP64, raise_on_not_converged=False):
+    o = hd_gmres_opts(restart, max_iters, rtol, use_x0, arnoldi)
     st = (hd_gmres_stats * nrhs)()
     allow = () if raise_on_not_converged else (HD_ERR_NOT_CONVERGED,)
     rc = _check("hd_gmres_solve", lib().hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, ct.byref(o), krylov_ptr, krylov_bytes,

@@ -172,7 +172,9 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
       s.ex0 = ax.e0; s.ex = ax.e1 - ax.e0; s.ey0 = ay.e0; s.ey = ay.e1 - ay.e0;
       s.ox0 = ax.o0; s.ox1 = ax.o1; s.oy0 = ay.o0; s.oy1 = ay.o1;
       s.ix = ix; s.iy = iy;
-      s.foff = foff; foff += (int64_t)s.ey * s.ex * s.ex;
+      s.ldm = (s.ex + 1) & ~1;
+      s.pad_ = 0;
+      s.foff = foff; foff += (int64_t)s.ey * s.ex * s.ldm;
       s.soff = soff; soff += (int64_t)s.ex * s.ey;
       s.woff = woff; woff += (int64_t)s.ex * s.ex;
       s.aoff = aoff; aoff += 2 * s.ex + 2 * s.ey + 2;
@@ -306,7 +308,8 @@ int hd_gmres_solve(hd_ctx *c, const void *b, void *x, int32_t nrhs, const hd_gmr
                    void *scratch, size_t scratch_bytes, hd_gmres_stats *stats, void *stream) {
   if (!c || !b || !x || !o || !kws || !scratch || !stats || nrhs < 1) return invalid("hd_gmres_solve: bad argument");
   if (!c->factored) return invalid("hd_gmres_solve: call hd_factor_subdomains first");
-  if (o->restart < 1 || o->max_iters < 0 || !(o->rtol >= 0)) return invalid("hd_gmres_solve: bad options");
+  if (o->restart < 1 || o->max_iters < 0 || !(o->rtol >= 0) || (o->arnoldi != HD_ARNOLDI_FP64 && o->arnoldi != HD_ARNOLDI_DS))
+    return invalid("hd_gmres_solve: bad options");
   size_t kb, sb;
   hd_query_workspace(c, 1, o->restart, nullptr, &kb, &sb);
   if (kbytes < kb) { set_error("hd_gmres_solve: krylov workspace too small"); return HD_ERR_OOM; }

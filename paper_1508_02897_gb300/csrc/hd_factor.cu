@@ -6,7 +6,9 @@
 // L_j (row j to row j-1) and U_j (row j to row j+1).  Block LU gives
 //     S_0 = D_0,   S_j = D_j - L_j S_{j-1}^{-1} U_{j-1},
 // and the solve needs only the S_j^{-1}, which are stored (m x m complex,
-// column-major: entry (r, c) at c*m + r) for every row j.
+// column-major with leading dimension ldm = m rounded up to even, so every
+// column starts on a 16-byte boundary: entry (r, c) at c*ldm + r) for every
+// row j.
 //
 // One CTA factorises one box.  Each S_j is inverted in place by Gauss-Jordan
 // elimination with partial pivoting done implicitly (rows are never moved: the
@@ -55,12 +57,13 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
   const double2 *ia2f = a2c + rows;
   T *W = work + s.woff;
   T *Fs = factor + s.foff;
-  const int64_t mm = (int64_t)m * m;
+  const int ldm = s.ldm;
+  const int64_t mm = (int64_t)m * m, slot_elems = (int64_t)m * ldm;
   bool bad = false;
 
   for (int j = 0; j < rows; ++j) {
     // ---- S_j = D_j - L_j S_{j-1}^{-1} U_{j-1} into W (column-major)
-    const T *prev = Fs + (j - 1) * mm;
+    const T *prev = Fs + (j - 1) * slot_elems;
     const double2 a2 = a2c[j], is = ia2f[j], in = ia2f[j + 1];
     const int gy = s.ey0 + j;
     for (int64_t idx = tid; idx < mm; idx += FT) {
@@ -83,7 +86,7 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
       if (j > 0) {
         double2 lr = cmul(a1c[r], is), lc = cmul(a1c[c], is);
         T l_r = mk<T>((R)lr.x, (R)lr.y), l_c = mk<T>((R)lc.x, (R)lc.y);
-        v = cfms(cmul(l_r, prev[idx]), l_c, v);
+        v = cfms(cmul(l_r, prev[(int64_t)c * ldm + r]), l_c, v);
       }
       W[idx] = v;
     }
@@ -190,10 +193,10 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
     }
 
     // ---- write S_j^{-1}[r][c] = W[p_r][q_c] (column-major) as factor row j
-    T *slot = Fs + j * mm;
+    T *slot = Fs + j * slot_elems;
     for (int64_t idx = tid; idx < mm; idx += FT) {
       int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
-      slot[idx] = W[(int64_t)qinv[c] * m + piv[r]];
+      slot[(int64_t)c * ldm + r] = W[(int64_t)qinv[c] * m + piv[r]];
     }
     __syncthreads();
   }

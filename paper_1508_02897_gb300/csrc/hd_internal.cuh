@@ -61,6 +61,8 @@ struct SubDev {
   int64_t woff;                  // offset of the factorisation working matrix (complex entries)
   int32_t aoff;                  // offset into the local PML table pool
   int32_t ix, iy;
+  int32_t ldm;                   // leading dimension of a stored S_j^{-1} (m rounded up to even)
+  int32_t pad_;
 };
 
 // One axis of the decomposition: per box column (or row) its extent and owned range.
@@ -130,5 +132,6 @@ cudaError_t launch_residual(hd_ctx *ctx, const double2 *b, const double2 *x, dou
 cudaError_t launch_rhs(hd_ctx *ctx, const double2 *f, double2 *b, cudaStream_t st);
 int run_factor(hd_ctx *ctx, void *factor, void *work, cudaStream_t st);
 int run_apply(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st);
+size_t subst_ring_bytes(const hd_ctx *ctx, int *stages);
 size_t factor_smem_bytes(int prec, int max_m);
 }  // namespace hd

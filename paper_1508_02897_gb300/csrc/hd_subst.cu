@@ -9,8 +9,16 @@
 //     x_last = w_last,        x_j = w_j - S_j^{-1} (U_j x_{j+1}),
 // leaving the local solution over the whole box (PML area included) in the
 // staging buffer.  Each step is one m x m complex GEMV against a stored
-// S_j^{-1}; thread t owns outputs a = t + ST*e and reads column-major entries
-// (b, a) for consecutive a, so every factor row is one coalesced stream.
+// S_j^{-1}, so the kernel streams 2 rows - 1 dense m x m blocks per box: it is
+// HBM-bound.  The stream of factor blocks does not depend on the vectors, so a
+// producer warp copies them ahead with bulk asynchronous copies
+// (cp.async.bulk, completion counted on an mbarrier) into a ring of NS shared
+// memory stages of CH columns each, across step boundaries; the consumer
+// warps accumulate y[a] = sum_b S[a][b] v[b] from shared memory (thread t owns
+// outputs a = t + CT*e) and release each stage on its "empty" mbarrier.
+// Every wait is bounded: on timeout the kernel flags ST_TIMEOUT, stops issuing
+// copies, lets every warp run to the end, and the producer waits for its own
+// copies still in flight before the CTA exits.
 //
 // k_gather then forms z cell by cell as a fixed-order sum over the (at most
 // 3 x 3, in practice 2 x 2) boxes whose extent covers the cell: deterministic,
@@ -19,142 +27,211 @@
 
 namespace hd {
 
-template <typename R, int ST, int NA>
-__global__ void __launch_bounds__(ST)
+constexpr uint32_t kWaitLimit = 1u << 24;   // try_wait rounds before a wait gives up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; false on timeout or when another warp already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && *abort_flag) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ void consumer_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+template <typename T> __host__ __device__ constexpr int chunk_cols() { return sizeof(T) == 8 ? 4 : 2; }
+
+// Shared memory layout: ring [NS][CH*ldm] | vs [ldmax] | full[NS] | empty[NS] | abort
+template <typename T>
+__host__ __device__ inline size_t subst_smem(int ns, int ldmax) {
+  size_t stage = (size_t)chunk_cols<T>() * ldmax * sizeof(T);
+  size_t o = (size_t)ns * stage + (size_t)ldmax * sizeof(T);
+  o = (o + 15) & ~(size_t)15;
+  return o + 2 * (size_t)ns * sizeof(uint64_t) + 16;
+}
+
+template <typename R, int CT, int NA>
+__global__ void __launch_bounds__(CT + 32)
 k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const C<R> *__restrict__ factor,
-        const double2 *__restrict__ rg, int NX, C<R> *__restrict__ staging) {
+        const double2 *__restrict__ rg, int NX, C<R> *__restrict__ staging, int NS, int ldmax, int32_t *status) {
   using T = C<R>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *vs = reinterpret_cast<T *>(smem_raw);  // [m] right-hand side of the current step
+  constexpr int CH = chunk_cols<T>();
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   const SubDev s = subs[blockIdx.x];
-  const int m = s.ex, rows = s.ey;
-  const int tid = threadIdx.x;
+  const int m = s.ex, rows = s.ey, ldm = s.ldm;
+  const size_t stage_elems = (size_t)CH * ldmax;
+  T *ring = reinterpret_cast<T *>(smem_raw);
+  T *vs = ring + (size_t)NS * stage_elems;
+  size_t off = ((size_t)NS * stage_elems + ldmax) * sizeof(T);
+  off = (off + 15) & ~(size_t)15;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + off);
+  uint64_t *empty = full + NS;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NS);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], CT / 32);
+    }
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  const int nck = (m + CH - 1) / CH;             // chunks per factor block
+  const int64_t total = (int64_t)(2 * rows - 1) * nck;
+  const int64_t slot_elems = (int64_t)m * ldm;
+  const T *Fs = factor + s.foff;
+
+  if (warp == CT / 32) {
+    // ---------------- producer warp: stream the factor blocks in use order
+    if (lane == 0) {
+      int64_t issued = 0;
+      bool ok = true;
+      for (int64_t it = 0; it < total && ok; ++it) {
+        const int st = (int)(it / nck), c = (int)(it - (int64_t)st * nck);
+        const int j = st < rows ? st : 2 * rows - 2 - st;
+        const int slot = (int)(it % NS);
+        const uint32_t ph = (uint32_t)((it / NS) & 1);
+        if (!mbar_wait(&empty[slot], ph ^ 1u, abort_flag)) { ok = false; break; }
+        const int cols = min(CH, m - c * CH);
+        const uint32_t bytes = (uint32_t)(cols * ldm * sizeof(T));
+        mbar_arrive_expect_tx(&full[slot], bytes);
+        bulk_g2s(ring + (size_t)slot * stage_elems, Fs + j * slot_elems + (int64_t)c * CH * ldm, bytes, &full[slot]);
+        issued = it + 1;
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(status, ST_TIMEOUT);
+      }
+      // no copy may still be landing in shared memory when the CTA exits
+      for (int64_t it = max((int64_t)0, issued - NS); it < issued; ++it)
+        mbar_wait(&full[it % NS], (uint32_t)((it / NS) & 1), abort_flag);
+    }
+    return;
+  }
+
+  // ---------------- consumer warps
   const double2 *a1c = pool + s.aoff;
   const double2 *a2c = a1c + 2 * m + 1;
   const double2 *ia2f = a2c + rows;
-  const T *Fs = factor + s.foff;
   T *stg = staging + s.soff;
-  const int64_t mm = (int64_t)m * m;
-
   T a1[NA], w[NA];
   bool ownx[NA];
 #pragma unroll
   for (int e = 0; e < NA; ++e) {
-    int a = tid + ST * e;
-    int gx = s.ex0 + a;
+    const int a = tid + CT * e;
+    const int gx = s.ex0 + a;
     ownx[e] = a < m && gx >= s.ox0 && gx < s.ox1;
-    double2 t = a < m ? a1c[a] : make_double2(0, 0);
+    const double2 t = a < m ? a1c[a] : make_double2(0, 0);
     a1[e] = mk<T>((R)t.x, (R)t.y);
     w[e] = mk<T>(0, 0);
   }
-
-  // ---- forward: restrict + w_j = S_j^{-1}(rho_j - L_j w_{j-1})
-  for (int j = 0; j < rows; ++j) {
-    const int gy = s.ey0 + j;
-    const bool owny = gy >= s.oy0 && gy < s.oy1;
-    const double2 isd = ia2f[j];
-    const T is = mk<T>((R)isd.x, (R)isd.y);
+  int64_t it = 0;
+  bool ok = true;
+  for (int st = 0; st < 2 * rows - 1; ++st) {
+    const bool fwd = st < rows;
+    const int j = fwd ? st : 2 * rows - 2 - st;
+    consumer_sync(CT);   // the previous step's reads of vs are done
+    if (fwd) {
+      const int gy = s.ey0 + j;
+      const bool owny = gy >= s.oy0 && gy < s.oy1;
+      const double2 isd = ia2f[j];
+      const T is = mk<T>((R)isd.x, (R)isd.y);
 #pragma unroll
-    for (int e = 0; e < NA; ++e) {
-      int a = tid + ST * e;
-      if (a < m) {
-        T rho = mk<T>(0, 0);
-        if (owny && ownx[e]) {
-          double2 rv = rg[(int64_t)gy * NX + s.ex0 + a];
-          rho = mk<T>((R)rv.x, (R)rv.y);
+      for (int e = 0; e < NA; ++e) {
+        const int a = tid + CT * e;
+        if (a < m) {
+          T rho = mk<T>(0, 0);
+          if (owny && ownx[e]) {
+            const double2 rv = rg[(int64_t)gy * NX + s.ex0 + a];
+            rho = mk<T>((R)rv.x, (R)rv.y);
+          }
+          vs[a] = j > 0 ? cfms(cmul(a1[e], is), w[e], rho) : rho;   // rho_j - L_j w_{j-1}
         }
-        T v = j > 0 ? cfms(cmul(a1[e], is), w[e], rho) : rho;   // rho - L_j w_{j-1}
-        vs[a] = v;
+      }
+    } else {
+      const double2 ind = ia2f[j + 1];
+      const T in = mk<T>((R)ind.x, (R)ind.y);
+#pragma unroll
+      for (int e = 0; e < NA; ++e) {
+        const int a = tid + CT * e;
+        if (a < m) vs[a] = cmul(cmul(a1[e], in), w[e]);             // U_j x_{j+1}
       }
     }
-    __syncthreads();
-    const T *S = Fs + j * mm;
+    consumer_sync(CT);
     T acc[NA];
 #pragma unroll
     for (int e = 0; e < NA; ++e) acc[e] = mk<T>(0, 0);
-    int b = 0;
-    for (; b + 8 <= m; b += 8) {
-      T mv[8][NA];
+    for (int c = 0; c < nck; ++c, ++it) {
+      const int slot = (int)(it % NS);
+      if (ok && !mbar_wait(&full[slot], (uint32_t)((it / NS) & 1), abort_flag)) {
+        ok = false;
+        *abort_flag = 1;
+        atomicOr(status, ST_TIMEOUT);
+      }
+      const T *blk = ring + (size_t)slot * stage_elems;
+      const int b0 = c * CH;
+      const int cols = min(CH, m - b0);
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int b = 0; b < CH; ++b) {
+        if (b < cols) {
+          const T vb = vs[b0 + b];
 #pragma unroll
-        for (int e = 0; e < NA; ++e) {
-          int a = tid + ST * e;
-          mv[u][e] = a < m ? S[(int64_t)(b + u) * m + a] : mk<T>(0, 0);
+          for (int e = 0; e < NA; ++e) {
+            const int a = tid + CT * e;
+            if (a < m) acc[e] = cfma(blk[b * ldm + a], vb, acc[e]);
+          }
         }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        T vb = vs[b + u];
-#pragma unroll
-        for (int e = 0; e < NA; ++e) acc[e] = cfma(mv[u][e], vb, acc[e]);
       }
-    }
-    for (; b < m; ++b) {
-      T vb = vs[b];
-#pragma unroll
-      for (int e = 0; e < NA; ++e) {
-        int a = tid + ST * e;
-        if (a < m) acc[e] = cfma(S[(int64_t)b * m + a], vb, acc[e]);
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
     }
 #pragma unroll
     for (int e = 0; e < NA; ++e) {
-      int a = tid + ST * e;
-      w[e] = acc[e];
-      if (a < m) stg[(int64_t)j * m + a] = acc[e];
-    }
-    __syncthreads();
-  }
-
-  // ---- back: x_j = w_j - S_j^{-1}(U_j x_{j+1}); w holds x_{j+1}
-  for (int j = rows - 2; j >= 0; --j) {
-    const double2 ind = ia2f[j + 1];
-    const T in = mk<T>((R)ind.x, (R)ind.y);
-#pragma unroll
-    for (int e = 0; e < NA; ++e) {
-      int a = tid + ST * e;
-      if (a < m) vs[a] = cmul(cmul(a1[e], in), w[e]);
-    }
-    __syncthreads();
-    const T *S = Fs + j * mm;
-    T acc[NA];
-#pragma unroll
-    for (int e = 0; e < NA; ++e) acc[e] = mk<T>(0, 0);
-    int b = 0;
-    for (; b + 8 <= m; b += 8) {
-      T mv[8][NA];
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-#pragma unroll
-        for (int e = 0; e < NA; ++e) {
-          int a = tid + ST * e;
-          mv[u][e] = a < m ? S[(int64_t)(b + u) * m + a] : mk<T>(0, 0);
-        }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        T vb = vs[b + u];
-#pragma unroll
-        for (int e = 0; e < NA; ++e) acc[e] = cfma(mv[u][e], vb, acc[e]);
-      }
-    }
-    for (; b < m; ++b) {
-      T vb = vs[b];
-#pragma unroll
-      for (int e = 0; e < NA; ++e) {
-        int a = tid + ST * e;
-        if (a < m) acc[e] = cfma(S[(int64_t)b * m + a], vb, acc[e]);
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < NA; ++e) {
-      int a = tid + ST * e;
+      const int a = tid + CT * e;
       if (a < m) {
-        T x = csub(stg[(int64_t)j * m + a], acc[e]);
-        w[e] = x;
-        stg[(int64_t)j * m + a] = x;
+        if (fwd) {
+          w[e] = acc[e];
+          stg[(int64_t)j * m + a] = acc[e];
+        } else {
+          const T x = csub(stg[(int64_t)j * m + a], acc[e]);
+          w[e] = x;
+          stg[(int64_t)j * m + a] = x;
+        }
       }
     }
-    __syncthreads();
   }
 }
 
@@ -184,24 +261,54 @@ k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const
   z[(int64_t)gy * NX + gx] = acc;
 }
 
+// Ring depth: as deep as shared memory allows for the CTAs that share an SM.
+template <typename T>
+static int ring_stages(const hd_ctx *ctx, int ldmax) {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = (ctx->nsub + sms - 1) / sms;
+  const size_t budget = (size_t)200 * 1024 / (size_t)std::max(1, per_sm);
+  const size_t stage = (size_t)chunk_cols<T>() * ldmax * sizeof(T);
+  int ns = (int)(budget / stage);
+  return std::min(32, std::max(2, ns));
+}
+
+size_t subst_ring_bytes(const hd_ctx *ctx, int *stages) {
+  const int ldmax = (ctx->max_m + 1) & ~1;
+  if (ctx->prec == HD_C64) {
+    int ns = ring_stages<float2>(ctx, ldmax);
+    if (stages) *stages = ns;
+    return subst_smem<float2>(ns, ldmax);
+  }
+  int ns = ring_stages<double2>(ctx, ldmax);
+  if (stages) *stages = ns;
+  return subst_smem<double2>(ns, ldmax);
+}
+
+template <typename R, int CT>
+static cudaError_t launch_subst(hd_ctx *ctx, const double2 *r, void *staging, cudaStream_t st) {
+  using T = C<R>;
+  const int ldmax = (ctx->max_m + 1) & ~1;
+  const int ns = ring_stages<T>(ctx, ldmax);
+  const size_t smem = subst_smem<T>(ns, ldmax);
+  cudaError_t e = cudaFuncSetAttribute(k_subst<R, CT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_subst<R, CT, 2><<<ctx->nsub, CT + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,
+                                                      reinterpret_cast<const T *>(ctx->factor), r, ctx->NX,
+                                                      reinterpret_cast<T *>(staging), ns, ldmax, ctx->d_status);
+  return cudaGetLastError();
+}
+
 template <typename R>
 static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st) {
-  using T = C<R>;
-  const T *F = reinterpret_cast<const T *>(ctx->factor);
-  T *S = reinterpret_cast<T *>(staging);
-  size_t smem = sizeof(T) * (size_t)ctx->max_m;
   tic(ctx, T_SUBST, st);
-  if (ctx->max_m <= 192)
-    k_subst<R, 96, 2><<<ctx->nsub, 96, smem, st>>>(ctx->d_subs, ctx->d_lpool, F, r, ctx->NX, S);
-  else
-    k_subst<R, 128, 2><<<ctx->nsub, 128, smem, st>>>(ctx->d_subs, ctx->d_lpool, F, r, ctx->NX, S);
+  cudaError_t e = ctx->max_m <= 192 ? launch_subst<R, 96>(ctx, r, staging, st) : launch_subst<R, 128>(ctx, r, staging, st);
   toc(ctx, T_SUBST, st, 1);
-  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   dim3 grid((ctx->NX + 255) / 256, ctx->NY);
   tic(ctx, T_GATHER, st);
   k_gather<R><<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
-                                    ctx->nby, S, z, ctx->NX);
+                                    ctx->nby, reinterpret_cast<const C<R> *>(staging), z, ctx->NX);
   toc(ctx, T_GATHER, st, 1);
   return cudaGetLastError();
 }

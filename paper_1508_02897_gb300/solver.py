@@ -88,7 +88,10 @@ class HelmholtzDDM:
             self._krylov[restart] = torch.empty(kb, dtype=torch.uint8, device=self.device)
         return self._krylov[restart]
 
-    def solve(self, b, restart: int = 50, rtol: float = 1e-8, max_iters: int = 1000, x0=None, out=None):
+    def solve(self, b, restart: int = 50, rtol: float = 1e-8, max_iters: int = 1000, x0=None, out=None,
+              arnoldi: str = "auto"):
+        """FGMRES solve of A x = b.  ``arnoldi``: "fp64", "ds" (double-single
+        Gram-Schmidt on the FP32 pipes) or "auto" (ds with c64 factors, fp64 with c128)."""
         b, nrhs = self._vec(b)
         if out is not None:
             x = out
@@ -99,8 +102,13 @@ class HelmholtzDDM:
         kws = self.krylov_workspace(restart)
         rc, stats = B.hd_gmres_solve(self.ctx, b.data_ptr(), x.data_ptr(), nrhs, restart, max_iters, rtol,
                                      kws.data_ptr(), kws.numel(), self.scratch.data_ptr(), self.scratch_bytes,
-                                     self._st(), use_x0=int(x0 is not None))
+                                     self._st(), use_x0=int(x0 is not None), arnoldi=self._arnoldi(arnoldi))
         return x, stats
+
+    def _arnoldi(self, mode: str) -> int:
+        if mode == "auto":
+            mode = "ds" if self.prec == B.HD_C64 else "fp64"
+        return {"fp64": B.HD_ARNOLDI_FP64, "ds": B.HD_ARNOLDI_DS}[mode]
 
     def set_profiling(self, on: bool = True):
         B.hd_set_profiling(self.ctx, on)
@@ -122,7 +130,7 @@ class HelmholtzDDM:
 
 def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: int, overlap: int,
                restart: int, rtol: float, max_iters: int = 5000, precision: str = "c64", cut_x=None, cut_y=None,
-               device: str = "cuda"):
+               device: str = "cuda", arnoldi: str = "auto"):
     """End-to-end solve from host arrays: velocity c [n][n] (float64) and source
     samples f [nrhs][n][n] (complex128), preferably in pinned memory.  Copies in,
     sets up the medium, factorises, forms b = J h^2 f, runs FGMRES and copies the
@@ -133,7 +141,7 @@ def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: i
     s = HelmholtzDDM(N, npml, omega, c_d, nbx, nby, overlap, precision=precision, cut_x=cut_x, cut_y=cut_y,
                      device=device)
     b = s.rhs(f_d)
-    x, stats = s.solve(b, restart=restart, rtol=rtol, max_iters=max_iters)
+    x, stats = s.solve(b, restart=restart, rtol=rtol, max_iters=max_iters, arnoldi=arnoldi)
     x_h = x.to("cpu")
     s.close()
     h2d = c_d.numel() * c_d.element_size() + f_d.numel() * f_d.element_size()

@@ -91,27 +91,30 @@ def test_precond_literal_ownership():
 
 
 @pytest.mark.parametrize("name", ["tiny", "ragged"])
-def test_gmres_fixed_steps_c128(name):
-    """Same FGMRES variant on both sides: the iterate after k steps agrees."""
+@pytest.mark.parametrize("arnoldi", ["fp64", "ds"])
+def test_gmres_fixed_steps_c128(name, arnoldi):
+    """Same FGMRES variant on both sides: the iterate after k steps agrees
+    (FP64 Gram-Schmidt, and the double-single one whose basis carries ~48 bits)."""
     case, c, g, A, P = oracle(name)
     s = gpu(name, "c128")
     f = W.gaussian_source(case["N"], case["npml"], 0.45, 0.55, 2.0 / case["N"])
     b = rhs_from_source(g, f)
     k = 4
     ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=3, rtol=1e-15, max_iters=k)
-    x, st = s.solve(torch.from_numpy(b), restart=3, rtol=1e-15, max_iters=k)
+    x, st = s.solve(torch.from_numpy(b), restart=3, rtol=1e-15, max_iters=k, arnoldi=arnoldi)
     assert st[0]["iters"] == ref.iters == k
     assert rel(x.cpu().numpy(), ref.x.reshape(g.n, g.n)) < 1e-9
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_gmres_converged_c128(name):
+@pytest.mark.parametrize("arnoldi", ["fp64", "ds"])
+def test_gmres_converged_c128(name, arnoldi):
     case, c, g, A, P = oracle(name)
     s = gpu(name, "c128")
     f = W.gaussian_source(case["N"], case["npml"], 0.5, 0.5, 2.0 / case["N"])
     b = rhs_from_source(g, f)
     ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=50, rtol=1e-8, max_iters=300)
-    x, st = s.solve(torch.from_numpy(b), restart=50, rtol=1e-8, max_iters=300)
+    x, st = s.solve(torch.from_numpy(b), restart=50, rtol=1e-8, max_iters=300, arnoldi=arnoldi)
     assert st[0]["converged"] == 1 and abs(st[0]["iters"] - ref.iters) <= 1
     xn = x.cpu().numpy().ravel()
     assert np.linalg.norm(b.ravel() - A @ xn) / np.linalg.norm(b) <= 1e-8
