@@ -142,6 +142,25 @@ typedef enum {
                            least squares and the true residual stay FP64               */
 } hd_arnoldi_mode;
 
+/* Preconditioner application that allocates nothing.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc
+ * when they apply the preconditioner (plug-ins whose host application owns the
+ * device heap, latency-bound loops where an allocation could synchronise the
+ * device, services that must keep a fixed device footprint after start-up).
+ * Same result as hd_apply_precond, but the staging vectors live in a fixed
+ * 64 MiB device array inside the library instead of a caller workspace; every
+ * GPU that loads the library holds that array until the process exits.  The
+ * first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  A problem whose staging vectors need more than 64 MiB
+ * (scratch_bytes of hd_query_workspace for the substitution) is refused with
+ * HD_ERR_OOM.  Every call shares the one array and it keeps the last call's
+ * contents (no entry is read before the same call writes it, so nothing needs
+ * clearing); calls whose work overlaps on the GPU -- other streams, contexts or
+ * threads -- race on it, so the caller must serialise them.  r_dev, z_dev as in
+ * hd_apply_precond; nrhs right-hand sides are processed one after another. */
+int hd_apply_precond_noalloc(hd_ctx *ctx, const void *r_dev, void *z_dev, int32_t nrhs, void *stream);
+
 typedef struct {
   int32_t restart;    /* Krylov vectors per cycle                                  */
   int32_t max_iters;  /* Arnoldi steps over all cycles                             */

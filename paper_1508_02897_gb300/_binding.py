@@ -64,6 +64,7 @@ _SIGS = {
     "hd_apply_precond": [_P, _P, _P, ct.c_int32, _P, ct.c_size_t, _P],
     "hd_gmres_solve": [_P, _P, _P, ct.c_int32, ct.POINTER(hd_gmres_opts), _P, ct.c_size_t, _P, ct.c_size_t,
                        ct.POINTER(hd_gmres_stats), _P],
+    "hd_apply_precond_noalloc": [_P, _P, _P, ct.c_int32, _P],
     "hd_set_profiling": [_P, ct.c_int32],
     "hd_get_timers": [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32, ct.c_int32, _P],
     "hd_check_status": [_P, ct.c_int32, _P],
@@ -142,6 +143,12 @@ def hd_rhs_from_source(ctx, f_ptr, b_ptr, nrhs, stream):
 
 def hd_apply_precond(ctx, r_ptr, z_ptr, nrhs, scratch_ptr, scratch_bytes, stream):
     _check("hd_apply_precond", lib().hd_apply_precond(ctx, r_ptr, z_ptr, nrhs, scratch_ptr, scratch_bytes, stream))
+
+
+def hd_apply_precond_noalloc(ctx, r_ptr, z_ptr, nrhs, stream):
+    """Preconditioner application whose staging lives in the library's fixed 64 MiB array
+    (for callers that cannot allocate device memory)."""
+    _check("hd_apply_precond_noalloc", lib().hd_apply_precond_noalloc(ctx, r_ptr, z_ptr, nrhs, stream))
 
 
 def hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, restart, max_iters, rtol, krylov_ptr, krylov_bytes, scratch_ptr,
