@@ -45,7 +45,13 @@ def parse():
     p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    p.add_argument("--config", default="precision", choices=W.CONFIGS)
+    p.add_argument("--config", default="precision", choices=W.CONFIGS + ("serving",))
+    p.add_argument("--rate", type=float, default=20.0, help="serving: mean arrivals per second")
+    p.add_argument("--window", type=float, default=10.0, help="serving: seconds of arrivals")
+    p.add_argument("--grids", default="256,512,1024,2048,4096", help="serving: grid sizes in the mix")
+    p.add_argument("--max-requests", type=int, default=0, help="serving: cap on the number of requests (0: none)")
+    p.add_argument("--slots", type=int, default=4)
+    p.add_argument("--budget-gb", type=float, default=160.0)
     p.add_argument("--precision", default="c64", choices=("c64", "c128"))
     p.add_argument("--restart", type=int, default=None)
     p.add_argument("--rtol", type=float, default=None)
@@ -55,6 +61,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-boxes", type=int, default=2)
     p.add_argument("--arnoldi", default="auto", choices=("auto", "fp64", "ds"))
+    p.add_argument("--nrhs", type=int, default=None, help="sources per solve (batching config: 64)")
+    p.add_argument("--group", type=int, default=16, help="sources solved together in lockstep")
+    p.add_argument("--single-sample", type=int, default=2, help="batching: sources also solved one at a time")
     return p.parse_args()
 
 
@@ -156,11 +165,13 @@ class Clocks:
 
 # ----------------------------------------------------------------------------- workload
 def workload(args, rank: int):
-    wl = W.make_workload(args.config, restart=args.restart, rtol=args.rtol)
+    nrhs = args.nrhs or (64 if args.config == "batching" else 1)
+    wl = W.make_workload(args.config, restart=args.restart, rtol=args.rtol, nrhs=nrhs)
     if rank > 0:  # every rank solves its own problem: same medium, its own source position
         rng = np.random.Generator(np.random.PCG64(7919 * rank + 17))
         xs, ys = rng.uniform(0.05, 0.95, size=2)
-        wl.f = W.gaussian_source(wl.N, wl.npml, xs, ys, 2.0 * wl.h)[None]
+        wl.f = np.stack([W.gaussian_source(wl.N, wl.npml, *rng.uniform(0.05, 0.95, size=2), 2.0 * wl.h)
+                         for _ in range(wl.nrhs)])
     return wl
 
 
@@ -170,17 +181,23 @@ def describe(wl, precision):
             f"to {wl.rtol:g}, {wl.nrhs} source(s)")
 
 
-def subst_bytes(wl, cs: int) -> int:
-    """Algorithmic HBM bytes of one k_subst launch (one preconditioner application):
-    every stored S_j^{-1} read once forward and once backward (the last row once),
-    the owned residual read once (FP64 complex), the staging vector written
-    forward, read and rewritten backward."""
-    tot = 16 * wl.n * wl.n
+def _rhs_per_cta(k):
+    return 8 if k >= 8 else (4 if k >= 4 else (2 if k >= 2 else 1))
+
+
+def subst_bytes(wl, cs: int, nrhs: int = 1) -> int:
+    """Algorithmic HBM bytes of one k_subst launch (one preconditioner application
+    to nrhs vectors): every stored S_j^{-1} read once forward and once backward (the
+    last row once) per group of right-hand sides sharing a CTA, the owned residual
+    read once (FP64 complex), the staging vector written forward, read and
+    rewritten backward."""
+    groups = -(-nrhs // _rhs_per_cta(nrhs))
+    tot = 16 * wl.n * wl.n * nrhs
     for iy in range(wl.nby):
         for ix in range(wl.nbx):
             m = _extent(wl.cut_x, ix, wl)
             rows = _extent(wl.cut_y, iy, wl)
-            tot += (2 * rows - 1) * m * m * cs + 3 * rows * m * cs
+            tot += (2 * rows - 1) * m * m * cs * groups + 3 * rows * m * cs * nrhs
     return tot
 
 
@@ -208,17 +225,24 @@ def run_ours(args, world, rank, local):
     f_d = torch.from_numpy(wl.f).to(dev)
     stream = torch.cuda.current_stream(dev)
 
-    def one_solve(precision, profile):
+    group = max(1, min(args.group, wl.nrhs))
+
+    def one_solve(precision, profile, f=None, grp=None):
+        f = f_d if f is None else f
+        grp = group if grp is None else grp
         s = HelmholtzDDM(wl.N, wl.npml, wl.omega, c_d, wl.nbx, wl.nby, wl.overlap, precision=precision,
                          cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev))
         s.set_profiling(profile)
         s.factor()
-        b = s.rhs(f_d)
-        x, st = s.solve(b, restart=wl.restart, rtol=wl.rtol, max_iters=args.max_iters,
-                        arnoldi=args.arnoldi if precision == args.precision else "fp64")
+        sts = []
+        for g0 in range(0, f.shape[0], grp):
+            b = s.rhs(f[g0:g0 + grp])
+            x, st = s.solve(b, restart=wl.restart, rtol=wl.rtol, max_iters=args.max_iters,
+                            arnoldi=args.arnoldi if precision == args.precision else "fp64")
+            sts.extend(st)
         tm = s.timers(reset=True)
         s.close()
-        return x, st[0], tm
+        return x, sts, tm
 
     for _ in range(args.warmup):
         one_solve(args.precision, False)
@@ -233,7 +257,7 @@ def run_ours(args, world, rank, local):
     for k in range(args.steps):
         _, st, tm = one_solve(args.precision, True)
         ev[k + 1].record(stream)
-        stats.append(st)
+        stats.extend(st)
         timers.append(tm)
     torch.cuda.synchronize(dev)
     barrier(world)
@@ -241,7 +265,7 @@ def run_ours(args, world, rank, local):
     step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     total_max_s = max_over_ranks(total_ms / 1e3, world)
-    solves = world * args.steps
+    solves = world * args.steps * wl.nrhs
     n_unk = wl.n * wl.n
     iters = [s["iters"] for s in stats]
     unk_iters = sum_over_ranks(sum(n_unk * it for it in iters), world) / total_max_s
@@ -252,7 +276,7 @@ def run_ours(args, world, rank, local):
     cls_n = {c: sum(t[c][1] for t in timers) for c in classes}
     launches = int(sum(cls_n.values()))
     cs = 8 if args.precision == "c64" else 16
-    sb = subst_bytes(wl, cs)
+    sb = subst_bytes(wl, cs, group)
     sub_avg_ms = cls_ms["subst"] / max(cls_n["subst"], 1)
     achieved = sb / (sub_avg_ms / 1e3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -278,6 +302,7 @@ def run_ours(args, world, rank, local):
     out = {
         "metric": METRIC, "value": solves / total_max_s, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_max_s * 1e3 / args.steps,
+        "sources_per_step": wl.nrhs, "lockstep_group": group,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "c64+f64" if args.precision == "c64" else "f64",
         "data": "synthetic (seeded random medium and Gaussian source; no dataset)",
@@ -289,7 +314,10 @@ def run_ours(args, world, rank, local):
         "unknown_iters_per_s": unk_iters,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "per_step": step_ms},
-        "iters": iters, "relres_true": [s["relres_true"] for s in stats],
+        "iters": iters if len(iters) <= 8 else {"mean": float(np.mean(iters)), "min": int(min(iters)),
+                                                  "max": int(max(iters))},
+        "relres_true": ([s["relres_true"] for s in stats] if len(stats) <= 8 else
+                        {"max": float(max(s["relres_true"] for s in stats))}),
         "converged": all(s["converged"] == 1 for s in stats),
         "breakdown_ms_per_step": {c: cls_ms[c] / args.steps for c in classes},
         "dominant_kernel_class": dominant,
@@ -305,8 +333,26 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
     }
 
+    # batching: the same sources solved one at a time (a sample), for the speedup of lockstep groups
+    if wl.nrhs > 1 and args.single_sample > 0:
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sst = []
+        for q in range(args.single_sample):
+            _, st1, _ = one_solve(args.precision, False, f=f_d[q:q + 1], grp=1)
+            sst.extend(st1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        t1 = e0.elapsed_time(e1) / 1e3
+        out["single_source_solves"] = {"value": args.single_sample / t1, "unit": "solves/s",
+                                       "note": "same workload, one source per solve (factorisation each time)",
+                                       "iters": [x["iters"] for x in sst],
+                                       "speedup_of_lockstep_groups": out["value"] / (args.single_sample / t1)}
+
     # plain FP64 comparison line on the same GPU
-    if args.fp64_steps > 0 and args.precision != "c128":
+    if args.fp64_steps > 0 and args.precision != "c128" and wl.nrhs == 1:
         torch.cuda.empty_cache()
         barrier(world)
         torch.cuda.synchronize(dev)
@@ -316,7 +362,7 @@ def run_ours(args, world, rank, local):
         st64 = []
         for _ in range(args.fp64_steps):
             _, st, tm = one_solve("c128", True)
-            st64.append((st, tm))
+            st64.append((st[0], tm))
         e1.record(stream)
         torch.cuda.synchronize(dev)
         t64 = max_over_ranks(e0.elapsed_time(e1) / 1e3, world)
@@ -332,7 +378,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.empty_cache()
 
     # end to end through the public API from pinned host buffers
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and wl.nrhs == 1:
         c_h = torch.from_numpy(wl.c).pin_memory()
         f_h = torch.from_numpy(wl.f).pin_memory()
         barrier(world)
@@ -350,7 +396,8 @@ def run_ours(args, world, rank, local):
 
     if rank == 0 and not args.no_cpu_baseline:
         it_ref = int(round(statistics.mean(iters)))
-        out["cpu_baseline"] = cpu_baseline(wl, it_ref, args.cpu_sample_boxes, "GPU FGMRES iteration count")
+        out["cpu_baseline"] = cpu_baseline(wl, it_ref, args.cpu_sample_boxes, "GPU FGMRES iteration count",
+                                           nrhs=wl.nrhs)
     return out
 
 
@@ -391,8 +438,63 @@ def _profile_traffic(wl, args):
 KERNEL_REV = "subst-v1"
 
 
+# ----------------------------------------------------------------------------- serving
+def _serving_restart(nb):
+    # the paper raised the GMRES restart with the boxes per direction (Sec. 3.1, Table 2)
+    return 30 if nb <= 8 else (60 if nb <= 16 else 120)
+
+
+def run_serving(args, world, rank, local):
+    """Poisson stream of solve requests through hd_submit/hd_poll (continuous batching)."""
+    import torch
+    from paper_1508_02897_gb300.build import build
+    from paper_1508_02897_gb300.solver import Server
+    build()
+    torch.cuda.set_device(local)
+    grids = tuple(int(g) for g in args.grids.split(","))
+    trace = W.poisson_trace(4 + 101 * rank, args.rate, args.window, grids=grids)
+    if args.max_requests:
+        trace = trace[:args.max_requests]
+    reqs = []
+    for q in trace:
+        N = q["N"]
+        wl = W.make_workload("tiny", N=N, nb=max(1, N // 128), medium=q["medium"], seed=q["seed"], nrhs=q["nrhs"],
+                             restart=_serving_restart(max(1, N // 128)), rtol=1e-6)
+        reqs.append((q["t"], wl))
+    srv = Server(hbm_budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots, device=local)
+    barrier(world)
+    t0 = time.perf_counter()
+    tickets = []
+    for t_arr, wl in reqs:
+        now = time.perf_counter() - t0
+        if t_arr > now:
+            time.sleep(t_arr - now)
+        tickets.append((srv.submit(wl.c, wl.f, wl.N, wl.npml, wl.omega, wl.nbx, wl.nby, wl.overlap, wl.restart,
+                                   wl.rtol, args.max_iters), wl))
+    lat, solves, ok, unk_it = [], 0, 0, 0.0
+    for t, wl in tickets:
+        x, stats, info = srv.poll(t)
+        lat.append(info["latency_s"])
+        solves += wl.nrhs
+        ok += sum(1 for s_ in stats if s_["converged"])
+        unk_it += wl.n * wl.n * sum(s_["iters"] for s_ in stats)
+    t_all = time.perf_counter() - t0
+    counters = srv.info()
+    srv.close()
+    t_max = max_over_ranks(t_all, world)
+    return {"metric": METRIC + " (serving)", "value": sum_over_ranks(solves, world) / t_max, "unit": "solves/s",
+            "n_gpus": world, "requests": len(reqs), "offered_req_per_s": args.rate,
+            "completed_req_per_s": len(reqs) / t_all, "converged_solves": ok, "total_solves": solves,
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(max(lat))},
+            "unknown_iters_per_s": unk_it / t_all, "wall_s": t_all, "slots": args.slots,
+            "budget_gb": args.budget_gb, "grids": list(grids), "window_s": args.window,
+            "peak_running": counters["peak_running"], "peak_bytes_in_use": counters["peak_bytes_in_use"],
+            "higher_is_better": True, "scaling": "weak", "dtype": "c64+f64", "data": "synthetic"}
+
+
 # ----------------------------------------------------------------------------- oracle (CPU) timing
-def cpu_baseline(wl, iters, n_boxes, iters_source):
+def cpu_baseline(wl, iters, n_boxes, iters_source, nrhs=1):
     """Times the FP64 CPU oracle on a bounded sample of one solve and
     extrapolates: per-box sparse LU and local solve (n_boxes sampled boxes),
     the global operator and one CGS2 Arnoldi step on a cropped grid, scaled by
@@ -426,11 +528,11 @@ def cpu_baseline(wl, iters, n_boxes, iters_source):
     h2 = V.conj() @ x
     x = x - V.T @ h2
     t_arn = (time.perf_counter() - t0) * (g.n * g.n) / (nc * nc)
-    t_solve = nb * t_fact + iters * (nb * t_sol + t_mv + t_arn)
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+    t_solve = nb * t_fact + nrhs * iters * (nb * t_sol + t_mv + t_arn)
+    return {"value": nrhs / t_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": (f"{len(pick)} of {nb} boxes factorised (sparse LU) and solved once, operator and one "
                        f"CGS2 step (j={jm}) on a {nc}^2 crop; extrapolated to {nb} boxes x {iters} iterations "
-                       f"({iters_source}), one thread"),
+                       f"({iters_source}) and {nrhs} source(s) sharing the factorisation, one thread"),
             "t_solve_s_extrapolated": t_solve, "t_factor_box_s": t_fact, "t_solve_box_s": t_sol}
 
 
@@ -480,7 +582,9 @@ def main():
             print(json.dumps(out), flush=True)
         return
     world, rank, local = dist_setup(args)
-    if True:
+    if args.config == "serving":
+        out = run_serving(args, world, rank, local)
+    else:
         out = run_ours(args, world, rank, local)
     if rank == 0 and out is not None:
         print(json.dumps(out), flush=True)

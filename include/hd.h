@@ -85,8 +85,9 @@ typedef struct hd_ctx hd_ctx;
  * decomposition, computes k^2 = (omega / c)^2 on the device from the velocity
  * c_dev (FP64, NY x NX, device memory, read during the call only), the global
  * and per-box PML stretching tables and the box tables.  Allocates its own
- * device tables (about 8 NX NY bytes plus O(boxes) ); synchronises `stream`
- * before returning.  On error *out is NULL. */
+ * device tables (about 8 NX NY bytes plus O(boxes)) stream-ordered on `stream`
+ * (cudaMallocAsync); synchronises `stream` before returning.  On error *out is
+ * NULL. */
 int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *decomp, const double *c_dev,
                     int32_t precision, void *stream);
 
@@ -94,9 +95,10 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *decomp, 
  *   factor_bytes  : the per-box Schur inverses written by hd_factor_subdomains
  *   krylov_bytes  : FGMRES bases V (restart+1 vectors) and Z (restart vectors),
  *                   two work vectors and the Hessenberg/reduction scratch, for
- *                   nrhs right-hand sides
- *   scratch_bytes : per-box staging of the local substitutions (apply) and the
- *                   per-box working matrix (factorisation)
+ *                   nrhs right-hand sides solved together
+ *   scratch_bytes : per-box staging of the local substitutions for nrhs
+ *                   right-hand sides (apply) or the per-box working matrix
+ *                   (factorisation), whichever is larger
  * Any output pointer may be NULL. */
 int hd_query_workspace(const hd_ctx *ctx, int32_t nrhs, int32_t restart, size_t *factor_bytes,
                        size_t *krylov_bytes, size_t *scratch_bytes);
@@ -129,8 +131,9 @@ int hd_rhs_from_source(hd_ctx *ctx, const void *f_dev, void *b_dev, int32_t nrhs
  * solution over the whole box, PML area included, and the sum runs in a fixed
  * order (deterministic).  r_dev, z_dev: complex128 [nrhs][NY][NX], must not
  * overlap.  Needs a prior hd_factor_subdomains.  scratch_dev: at least
- * scratch_bytes of hd_query_workspace for nrhs = 1 (right-hand sides are
- * processed one after another). */
+ * scratch_bytes of hd_query_workspace for nrhs = 1; with room for g right-hand
+ * sides they are processed g at a time, each factor block read once per group
+ * (up to 8 right-hand sides per CTA). */
 int hd_apply_precond(hd_ctx *ctx, const void *r_dev, void *z_dev, int32_t nrhs, void *scratch_dev,
                      size_t scratch_bytes, void *stream);
 
@@ -158,7 +161,7 @@ typedef enum {
  * contents (no entry is read before the same call writes it, so nothing needs
  * clearing); calls whose work overlaps on the GPU -- other streams, contexts or
  * threads -- race on it, so the caller must serialise them.  r_dev, z_dev as in
- * hd_apply_precond; nrhs right-hand sides are processed one after another. */
+ * hd_apply_precond; right-hand sides are processed in groups that fit the array. */
 int hd_apply_precond_noalloc(hd_ctx *ctx, const void *r_dev, void *z_dev, int32_t nrhs, void *stream);
 
 typedef struct {
@@ -186,8 +189,11 @@ typedef struct {
  * b - A x decides convergence.  Blocking: returns when every right-hand side
  * has converged or failed, with stats_host[nrhs] filled in.  b_dev, x_dev:
  * complex128 [nrhs][NY][NX]; x_dev is the output (and the start when use_x0).
- * krylov_dev/scratch_dev sized by hd_query_workspace for (1, restart): the
- * right-hand sides are solved one after another. */
+ * The nrhs right-hand sides are solved together in lockstep (one independent
+ * FGMRES each; every preconditioner launch serves all of them, a converged one
+ * stops while the others go on); krylov_dev and scratch_dev must be sized by
+ * hd_query_workspace for (nrhs, restart).  Returns HD_ERR_NOT_CONVERGED if any
+ * right-hand side missed rtol within max_iters. */
 int hd_gmres_solve(hd_ctx *ctx, const void *b_dev, void *x_dev, int32_t nrhs, const hd_gmres_opts *opts,
                    void *krylov_dev, size_t krylov_bytes, void *scratch_dev, size_t scratch_bytes,
                    hd_gmres_stats *stats_host, void *stream);
@@ -207,7 +213,63 @@ int hd_get_timers(hd_ctx *ctx, double *ms, int64_t *launches, int32_t n, int32_t
  * resets it. */
 int hd_check_status(hd_ctx *ctx, int32_t clear, void *stream);
 
-/* Frees the context's own device tables (not the caller's workspaces). */
+/* ---------------------------------------------------------------- serving
+ * Continuous batching of solve requests on one GPU (no counterpart in the
+ * paper, whose solves ran one at a time on a cluster).  A server owns
+ * max_slots worker threads, each with its own non-blocking stream.  A
+ * submitted request waits in a first-come-first-served queue until a slot is
+ * free and its device memory (context tables, factors, Krylov bases, staging
+ * and vectors; all from the stream-ordered allocator, so no allocation
+ * synchronises the device) fits in what is left of hbm_budget_bytes; admitted
+ * requests run concurrently and their kernels overlap on the device.  Each
+ * request keeps its factors and Krylov bases resident until it completes.  A
+ * request whose nrhs right-hand sides do not fit the budget together is solved
+ * in lockstep sub-batches that do.  Results do not depend on what else runs. */
+typedef struct hd_server hd_server;
+
+typedef struct {
+  double queue_s;        /* submit -> admission                                      */
+  double run_s;          /* admission -> completion                                  */
+  double latency_s;      /* submit -> completion                                     */
+  uint64_t device_bytes; /* device memory reserved while running                     */
+  int32_t batch;         /* right-hand sides per lockstep sub-batch                  */
+} hd_request_info;
+
+typedef struct {
+  int32_t queued, running, peak_running;
+  uint64_t completed, bytes_in_use, peak_bytes_in_use, budget_bytes;
+} hd_server_counters;
+
+/* Starts a server on CUDA device `device` with max_slots (1..64) concurrent
+ * requests and a device memory budget in bytes. */
+int hd_server_create(hd_server **out, size_t hbm_budget_bytes, int32_t max_slots, int32_t device);
+
+/* Queues one solve: medium c_host (FP64 velocity, NY x NX), sources f_host
+ * (complex128 [nrhs][NY][NX], turned into b = J h^2 f on the device), FGMRES
+ * options, output x_host (complex128 [nrhs][NY][NX]).  The three host buffers
+ * are the caller's and must stay valid until hd_poll returns something other
+ * than HD_PENDING for the ticket.  The grid/decomposition structs and cut
+ * arrays are copied.  HD_ERR_OOM if one right-hand side alone exceeds the
+ * budget. */
+int hd_submit(hd_server *srv, const hd_grid *grid, const hd_decomp *decomp, const double *c_host, const void *f_host,
+              int32_t nrhs, int32_t precision, const hd_gmres_opts *opts, void *x_host, uint64_t *ticket);
+
+/* Waits up to timeout_us (0: do not wait, < 0: wait forever) for a ticket.
+ * HD_PENDING while it is queued or running; otherwise the request's status,
+ * with stats[nrhs] and *info (either may be NULL) filled in and the ticket
+ * released. */
+int hd_poll(hd_server *srv, uint64_t ticket, hd_gmres_stats *stats, hd_request_info *info, int64_t timeout_us);
+
+/* Snapshot of the server's counters. */
+int hd_server_info(hd_server *srv, hd_server_counters *out);
+
+/* Stops the server: requests already running finish, queued ones are dropped
+ * (their tickets become invalid), the worker threads are joined. */
+int hd_server_destroy(hd_server *srv);
+
+/* Frees the context's own device tables (not the caller's workspaces), stream
+ * ordered after the work queued on the stream given to hd_setup_medium (which
+ * must still exist); does not synchronise the device. */
 int hd_destroy(hd_ctx *ctx);
 
 /* Message of the last error on the calling thread ("" if none). */

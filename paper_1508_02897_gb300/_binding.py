@@ -47,6 +47,23 @@ class hd_gmres_stats(ct.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hd_request_info(ct.Structure):
+    _fields_ = [("queue_s", ct.c_double), ("run_s", ct.c_double), ("latency_s", ct.c_double),
+                ("device_bytes", ct.c_uint64), ("batch", ct.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hd_server_counters(ct.Structure):
+    _fields_ = [("queued", ct.c_int32), ("running", ct.c_int32), ("peak_running", ct.c_int32),
+                ("completed", ct.c_uint64), ("bytes_in_use", ct.c_uint64), ("peak_bytes_in_use", ct.c_uint64),
+                ("budget_bytes", ct.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class HDError(RuntimeError):
     def __init__(self, fn, code, msg):
         super().__init__(f"{fn} failed with {STATUS_NAMES.get(code, code)}: {msg}")
@@ -69,6 +86,12 @@ _SIGS = {
     "hd_get_timers": [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32, ct.c_int32, _P],
     "hd_check_status": [_P, ct.c_int32, _P],
     "hd_destroy": [_P],
+    "hd_server_create": [ct.POINTER(_P), ct.c_size_t, ct.c_int32, ct.c_int32],
+    "hd_submit": [_P, ct.POINTER(hd_grid), ct.POINTER(hd_decomp), _P, _P, ct.c_int32, ct.c_int32,
+                  ct.POINTER(hd_gmres_opts), _P, ct.POINTER(ct.c_uint64)],
+    "hd_poll": [_P, ct.c_uint64, ct.POINTER(hd_gmres_stats), ct.POINTER(hd_request_info), ct.c_int64],
+    "hd_server_info": [_P, ct.POINTER(hd_server_counters)],
+    "hd_server_destroy": [_P],
     "hd_last_error": [],
     "hd_version": [],
 }
@@ -187,3 +210,45 @@ def hd_last_error():
 
 def hd_version():
     return lib().hd_version().decode()
+
+
+def hd_server_create(hbm_budget_bytes, max_slots, device=0):
+    srv = _P()
+    _check("hd_server_create", lib().hd_server_create(ct.byref(srv), int(hbm_budget_bytes), int(max_slots), int(device)))
+    return srv
+
+
+def hd_submit(srv, nx, ny, npml, h, omega, c_ptr, f_ptr, nrhs, precision, restart, max_iters, rtol, x_ptr, nbx, nby,
+              overlap, cut_x=None, cut_y=None, own_global_pml=1, arnoldi=HD_ARNOLDI_FP64, sigma0_over_omega=20.0,
+              pml_power=2):
+    """Queues a solve; host buffers (c, f, x) must stay alive until hd_poll reports completion."""
+    g = hd_grid(nx, ny, npml, h, omega, sigma0_over_omega, pml_power)
+    kx, px = _cuts(cut_x)
+    ky, py = _cuts(cut_y)
+    d = hd_decomp(nbx, nby, overlap, px, py, own_global_pml)
+    o = hd_gmres_opts(restart, max_iters, rtol, 0, arnoldi)
+    t = ct.c_uint64()
+    _check("hd_submit", lib().hd_submit(srv, ct.byref(g), ct.byref(d), c_ptr, f_ptr, nrhs, precision, ct.byref(o),
+                                        x_ptr, ct.byref(t)))
+    return t.value
+
+
+def hd_poll(srv, ticket, nrhs, timeout_us=-1):
+    """Returns (status, stats list, info dict); status HD_PENDING while queued or running."""
+    st = (hd_gmres_stats * nrhs)()
+    info = hd_request_info()
+    rc = lib().hd_poll(srv, ct.c_uint64(ticket), st, ct.byref(info), int(timeout_us))
+    if rc == HD_PENDING:
+        return rc, None, None
+    _check("hd_poll", rc, allow=(HD_ERR_NOT_CONVERGED,))
+    return rc, [x.as_dict() for x in st], info.as_dict()
+
+
+def hd_server_info(srv):
+    c = hd_server_counters()
+    _check("hd_server_info", lib().hd_server_info(srv, ct.byref(c)))
+    return c.as_dict()
+
+
+def hd_server_destroy(srv):
+    _check("hd_server_destroy", lib().hd_server_destroy(srv))

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhd.so")
-UNITS = ["hd_api", "hd_stencil", "hd_factor", "hd_subst", "hd_krylov", "hd_noalloc"]
+UNITS = ["hd_api", "hd_stencil", "hd_factor", "hd_subst", "hd_krylov", "hd_noalloc", "hd_server"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -59,7 +59,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
             if log:
                 sys.stderr.write(log)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
+        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lpthread"]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"link of libhd.so failed:\n{p.stdout}\n{p.stderr}")

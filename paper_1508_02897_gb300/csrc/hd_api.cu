@@ -69,25 +69,21 @@ int collect_timers(hd_ctx *ctx) {
   return HD_OK;
 }
 
-size_t krylov_bytes(int64_t n, int restart);
-int run_gmres_one(hd_ctx *ctx, const double2 *b, double2 *x, const hd_gmres_opts *o, void *kws, void *scratch,
-                  hd_gmres_stats *stats, double *host_stat, cudaStream_t st);
 
 static void free_ctx(hd_ctx *c) {
   if (!c) return;
-  cudaFree(c->d_k2);
-  cudaFree(c->d_gax_c);
-  cudaFree(c->d_giax_f);
-  cudaFree(c->d_gay_c);
-  cudaFree(c->d_giay_f);
-  cudaFree(c->d_lpool);
-  cudaFree(c->d_subs);
-  cudaFree(c->d_axx);
-  cudaFree(c->d_axy);
-  cudaFree(c->d_nearx);
-  cudaFree(c->d_neary);
-  cudaFree(c->d_status);
-  if (c->host_stat) cudaFreeHost(c->host_stat);
+  if (c->d_k2) cudaFreeAsync(c->d_k2, c->stream);
+  if (c->d_gax_c) cudaFreeAsync(c->d_gax_c, c->stream);
+  if (c->d_giax_f) cudaFreeAsync(c->d_giax_f, c->stream);
+  if (c->d_gay_c) cudaFreeAsync(c->d_gay_c, c->stream);
+  if (c->d_giay_f) cudaFreeAsync(c->d_giay_f, c->stream);
+  if (c->d_lpool) cudaFreeAsync(c->d_lpool, c->stream);
+  if (c->d_subs) cudaFreeAsync(c->d_subs, c->stream);
+  if (c->d_axx) cudaFreeAsync(c->d_axx, c->stream);
+  if (c->d_axy) cudaFreeAsync(c->d_axy, c->stream);
+  if (c->d_nearx) cudaFreeAsync(c->d_nearx, c->stream);
+  if (c->d_neary) cudaFreeAsync(c->d_neary, c->stream);
+  if (c->d_status) cudaFreeAsync(c->d_status, c->stream);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
@@ -155,6 +151,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   c->NX = grid->nx + 2 * grid->npml; c->NY = grid->ny + 2 * grid->npml;
   c->h = grid->h; c->omega = grid->omega; c->s0 = grid->sigma0_over_omega; c->power = grid->pml_power;
   c->prec = precision;
+  c->stream = st;
   c->nbx = dec->nbx; c->nby = dec->nby; c->overlap = dec->overlap; c->own_global_pml = dec->own_global_pml ? 1 : 0;
   std::vector<int32_t> nearx, neary;
   int rc = axis_ranges(grid->nx, grid->npml, dec->nbx, dec->overlap, dec->cut_x, c->own_global_pml, c->axx, nearx, "x");
@@ -189,8 +186,8 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   const int64_t n = (int64_t)c->NX * c->NY;
 #define ALLOC(p, bytes)                                                     \
   do {                                                                      \
-    cudaError_t e_ = cudaMalloc(&(p), (bytes));                             \
-    if (e_ != cudaSuccess) { free_ctx(c); return cuda_fail(e_, "cudaMalloc"); } \
+    cudaError_t e_ = cudaMallocAsync((void **)&(p), (bytes), st);          \
+    if (e_ != cudaSuccess) { free_ctx(c); return cuda_fail(e_, "cudaMallocAsync"); } \
   } while (0)
   ALLOC(c->d_k2, sizeof(double) * n);
   ALLOC(c->d_gax_c, sizeof(double2) * c->NX);
@@ -205,8 +202,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   ALLOC(c->d_neary, sizeof(int32_t) * c->NY);
   ALLOC(c->d_status, sizeof(int32_t));
 #undef ALLOC
-  cudaError_t e = cudaMallocHost(&c->host_stat, 8 * sizeof(double));
-  if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "cudaMallocHost"); }
+  cudaError_t e;
 #define CP(dst, src, bytes)                                                                        \
   do {                                                                                             \
     cudaError_t e_ = cudaMemcpyAsync((dst), (src), (bytes), cudaMemcpyHostToDevice, st);           \
@@ -237,8 +233,8 @@ int hd_query_workspace(const hd_ctx *c, int32_t nrhs, int32_t restart, size_t *f
   if (nrhs < 1 || restart < 1) return invalid("hd_query_workspace: nrhs and restart must be >= 1");
   size_t cs = c->prec == HD_C64 ? sizeof(float2) : sizeof(double2);
   if (factor_bytes) *factor_bytes = cs * (size_t)c->factor_elems;
-  if (scratch_bytes) *scratch_bytes = cs * (size_t)std::max(c->staging_elems, c->work_elems);
-  if (krylov_bytes_out) *krylov_bytes_out = krylov_bytes((int64_t)c->NX * c->NY, restart);
+  if (scratch_bytes) *scratch_bytes = cs * (size_t)std::max(c->staging_elems * (int64_t)nrhs, c->work_elems);
+  if (krylov_bytes_out) *krylov_bytes_out = krylov_bytes((int64_t)c->NX * c->NY, restart, nrhs);
   return HD_OK;
 }
 
@@ -265,12 +261,10 @@ int hd_matvec(hd_ctx *c, const void *x, void *y, int32_t nrhs, void *stream) {
   if (!aligned16(x) || !aligned16(y)) return invalid("hd_matvec: vectors must be 16-byte aligned");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t n = (int64_t)c->NX * c->NY;
-  for (int r = 0; r < nrhs; ++r) {
-    tic(c, T_MATVEC, st);
-    cudaError_t e = launch_matvec(c, reinterpret_cast<const double2 *>(x) + r * n, reinterpret_cast<double2 *>(y) + r * n, st);
-    toc(c, T_MATVEC, st, 1);
-    if (e != cudaSuccess) return cuda_fail(e, "hd_matvec");
-  }
+  tic(c, T_MATVEC, st);
+  cudaError_t e = launch_matvec(c, reinterpret_cast<const double2 *>(x), n, reinterpret_cast<double2 *>(y), n, nrhs, st);
+  toc(c, T_MATVEC, st, 1);
+  if (e != cudaSuccess) return cuda_fail(e, "hd_matvec");
   return HD_OK;
 }
 
@@ -291,14 +285,16 @@ int hd_apply_precond(hd_ctx *c, const void *r, void *z, int32_t nrhs, void *scra
                      void *stream) {
   if (!c || !r || !z || !scratch || nrhs < 1) return invalid("hd_apply_precond: bad argument");
   if (!c->factored) return invalid("hd_apply_precond: call hd_factor_subdomains first");
-  size_t sb;
-  hd_query_workspace(c, 1, 1, nullptr, nullptr, &sb);
-  if (scratch_bytes < sb) { set_error("hd_apply_precond: scratch workspace too small"); return HD_ERR_OOM; }
+  const size_t per = (c->prec == HD_C64 ? sizeof(float2) : sizeof(double2)) * (size_t)c->staging_elems;
+  if (scratch_bytes < per) { set_error("hd_apply_precond: scratch workspace too small"); return HD_ERR_OOM; }
   if (!aligned16(r) || !aligned16(z) || !aligned16(scratch)) return invalid("hd_apply_precond: buffers must be 16-byte aligned");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t n = (int64_t)c->NX * c->NY;
-  for (int k = 0; k < nrhs; ++k) {
-    int rc = run_apply(c, reinterpret_cast<const double2 *>(r) + k * n, reinterpret_cast<double2 *>(z) + k * n, scratch, st);
+  const int group = (int)std::min<size_t>((size_t)nrhs, scratch_bytes / per);   // right-hand sides per launch
+  for (int k = 0; k < nrhs; k += group) {
+    const int g = std::min(group, nrhs - k);
+    int rc = run_apply(c, reinterpret_cast<const double2 *>(r) + k * n, n, reinterpret_cast<double2 *>(z) + k * n, n, g,
+                       scratch, st);
     if (rc) return rc;
   }
   return HD_OK;
@@ -311,30 +307,26 @@ int hd_gmres_solve(hd_ctx *c, const void *b, void *x, int32_t nrhs, const hd_gmr
   if (o->restart < 1 || o->max_iters < 0 || !(o->rtol >= 0) || (o->arnoldi != HD_ARNOLDI_FP64 && o->arnoldi != HD_ARNOLDI_DS))
     return invalid("hd_gmres_solve: bad options");
   size_t kb, sb;
-  hd_query_workspace(c, 1, o->restart, nullptr, &kb, &sb);
-  if (kbytes < kb) { set_error("hd_gmres_solve: krylov workspace too small"); return HD_ERR_OOM; }
-  if (scratch_bytes < sb) { set_error("hd_gmres_solve: scratch workspace too small"); return HD_ERR_OOM; }
+  hd_query_workspace(c, nrhs, o->restart, nullptr, &kb, &sb);
+  if (kbytes < kb) { set_error("hd_gmres_solve: krylov workspace too small for nrhs right-hand sides"); return HD_ERR_OOM; }
+  if (scratch_bytes < sb) { set_error("hd_gmres_solve: scratch workspace too small for nrhs right-hand sides"); return HD_ERR_OOM; }
   if (!aligned16(b) || !aligned16(x) || !aligned16(kws) || !aligned16(scratch))
     return invalid("hd_gmres_solve: buffers must be 16-byte aligned");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int64_t n = (int64_t)c->NX * c->NY;
-  int worst = HD_OK;
-  for (int k = 0; k < nrhs; ++k) {
-    std::memset(&stats[k], 0, sizeof(hd_gmres_stats));
-    int rc = run_gmres_one(c, reinterpret_cast<const double2 *>(b) + k * n, reinterpret_cast<double2 *>(x) + k * n, o,
-                           kws, scratch, &stats[k], c->host_stat, st);
-    stats[k].status = rc;
-    if (rc == HD_ERR_CUDA) return rc;
-    if (rc && !worst) worst = rc;
-  }
+  std::memset(stats, 0, sizeof(hd_gmres_stats) * nrhs);
+  int rc = run_gmres_batch(c, reinterpret_cast<const double2 *>(b), reinterpret_cast<double2 *>(x), nrhs, o, kws,
+                           scratch, stats, st);
+  if (rc == HD_ERR_CUDA) return rc;
   int32_t status = 0;
-  cudaError_t e = cudaMemcpyAsync(c->host_stat, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(c->host_stat.data(), c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "hd_gmres_solve status");
-  std::memcpy(&status, c->host_stat, sizeof(int32_t));
+  std::memcpy(&status, c->host_stat.data(), sizeof(int32_t));
+  if (status & ST_TIMEOUT) { set_error("hd_gmres_solve: a bounded device wait gave up"); return HD_ERR_TIMEOUT; }
   if (status) { set_error("hd_gmres_solve: a zero pivot or non-finite value was flagged on the device"); return HD_ERR_NUMERIC; }
-  if (worst == HD_ERR_NOT_CONVERGED) set_error("hd_gmres_solve: not converged within max_iters");
-  return worst;
+  if (rc == HD_ERR_NOT_CONVERGED) set_error("hd_gmres_solve: not converged within max_iters");
+  if (rc == HD_ERR_NUMERIC) set_error("hd_gmres_solve: non-finite value in the Arnoldi process");
+  return rc;
 }
 
 int hd_set_profiling(hd_ctx *c, int32_t on) {
@@ -360,11 +352,11 @@ int hd_get_timers(hd_ctx *c, double *ms, int64_t *launches, int32_t n, int32_t r
 int hd_check_status(hd_ctx *c, int32_t clear, void *stream) {
   if (!c) return invalid("hd_check_status: NULL context");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(c->host_stat, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+  cudaError_t e = cudaMemcpyAsync(c->host_stat.data(), c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "hd_check_status");
   int32_t status;
-  std::memcpy(&status, c->host_stat, sizeof(int32_t));
+  std::memcpy(&status, c->host_stat.data(), sizeof(int32_t));
   if (clear) {
     e = cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return cuda_fail(e, "hd_check_status clear");
@@ -376,8 +368,7 @@ int hd_check_status(hd_ctx *c, int32_t clear, void *stream) {
 
 int hd_destroy(hd_ctx *c) {
   if (!c) return HD_OK;
-  cudaDeviceSynchronize();
-  free_ctx(c);
+  free_ctx(c);   // stream-ordered frees after the work queued on the set-up stream
   return HD_OK;
 }
 

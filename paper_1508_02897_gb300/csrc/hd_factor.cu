@@ -8,34 +8,37 @@
 // and the solve needs only the S_j^{-1}, which are stored (m x m complex,
 // column-major with leading dimension ldm = m rounded up to even, so every
 // column starts on a 16-byte boundary: entry (r, c) at c*ldm + r) for every
-// row j.
+// row j.  The matrix is complex symmetric, so U_{j-1} = L_j.
 //
 // One CTA factorises one box.  Each S_j is inverted in place by Gauss-Jordan
-// elimination with partial pivoting done implicitly (rows are never moved: the
-// pivot of step k is the largest unpivoted entry of column k).  The elimination
-// is blocked by panels of PB columns: the panel is eliminated in shared memory,
-// recording for every step its multiplier column and pivot, and every other
-// column is then streamed once through registers (one warp per column) while
-// the PB recorded steps are applied to it.  If the pivot of step k sits in
-// row p_k and q = p^{-1}, the in-place result W satisfies
-//     S^{-1}[r][c] = W[p_r][q_c],
-// which is how the inverse is written out.
+// elimination with partial pivoting done implicitly (rows never move: the
+// pivot of step k is the largest unpivoted entry of column k), blocked by
+// panels of PB columns:
+//   1. the panel is eliminated in shared memory, one thread per row;
+//   2. with T the product of the panel's PB elementary steps and p_t its pivot
+//      rows, the eliminated panel column t equals T e_{p_t}, and T leaves
+//      e_i unchanged for every non-pivot row i, so every other column c becomes
+//          c' = c with rows p_t zeroed  +  sum_t c[p_t] * panel[:, t],
+//      a rank-PB update done as a register-tiled complex GEMM (4 x 4 tiles).
+// If the pivot of step k sits in row p_k and q = p^{-1}, the in-place result W
+// satisfies S^{-1}[r][c] = W[p_r][q_c], which is how the inverse is written out.
 #include "hd_internal.cuh"
 
 namespace hd {
 
 constexpr int FT = 512;        // threads per CTA
-constexpr int FWARPS = FT / 32;
 constexpr int PB = 16;         // panel width
+constexpr int TR = 4, TC = 4;  // GEMM tile of the trailing update (rows x columns)
 
+// Shared memory: panel [PB][m] | B [PB][m] | lS [m] | X [PB] | IPV [PB] | piv, qinv, mark [m] ints
 size_t factor_smem_bytes(int prec, int max_m) {
   size_t cs = prec == HD_C64 ? sizeof(float2) : sizeof(double2);
-  return cs * (2 * (size_t)PB * max_m + 2 * PB) + sizeof(int) * 3 * (size_t)max_m;
+  return cs * (2 * (size_t)PB * max_m + max_m + 2 * PB) + sizeof(int) * 3 * (size_t)max_m + 16;
 }
 
 template <typename T> __device__ __forceinline__ auto cabs2(T a) { return a.x * a.x + a.y * a.y; }
 
-template <typename R, int NPL>
+template <typename R>
 __global__ void __launch_bounds__(FT, 1)
 k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const double *__restrict__ k2, int NX,
          double h2, C<R> *__restrict__ factor, C<R> *__restrict__ work, int32_t *status) {
@@ -43,13 +46,14 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SubDev s = subs[blockIdx.x];
   const int m = s.ex, rows = s.ey;
-  T *P = reinterpret_cast<T *>(smem_raw);   // [PB][m] panel
-  T *F = P + PB * m;                         // [PB][m] multiplier columns
-  T *X = F + PB * m;                         // [PB] pivot-row values of the panel
+  T *P = reinterpret_cast<T *>(smem_raw);   // [PB][m] panel (eliminated in place)
+  T *Bm = P + PB * m;                        // [PB][m] pivot rows of the other columns
+  T *lS = Bm + PB * m;                       // [m] coupling L_j of the current grid row
+  T *X = lS + m;                             // [PB] pivot-row values of the panel
   T *IPV = X + PB;                           // [PB] reciprocal pivots
   int *piv = reinterpret_cast<int *>(IPV + PB);  // [m] pivot row of step k
   int *qinv = piv + m;                           // [m] step at which row r was pivot
-  int *done = qinv + m;                          // [m]
+  int *mark = qinv + m;                          // [m] panel start at which row r became pivot (-1: not yet)
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double2 *a1c = pool + s.aoff;
   const double2 *ia1f = a1c + m;
@@ -62,131 +66,139 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
   bool bad = false;
 
   for (int j = 0; j < rows; ++j) {
-    // ---- S_j = D_j - L_j S_{j-1}^{-1} U_{j-1} into W (column-major)
+    // ---- S_j = D_j - L_j S_{j-1}^{-1} L_j into W (column-major)
     const T *prev = Fs + (j - 1) * slot_elems;
     const double2 a2 = a2c[j], is = ia2f[j], in = ia2f[j + 1];
     const int gy = s.ey0 + j;
+    for (int r = tid; r < m; r += FT) {
+      const double2 l = cmul(a1c[r], is);   // south coupling of row j (= north coupling of row j-1)
+      lS[r] = mk<T>((R)l.x, (R)l.y);
+      mark[r] = -1;
+    }
+    __syncthreads();
     for (int64_t idx = tid; idx < mm; idx += FT) {
-      int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
+      const int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
       T v = mk<T>(0, 0);
       if (r == c) {
-        double2 a1 = a1c[r];
-        double2 cw = cmul(a2, ia1f[r]), ce = cmul(a2, ia1f[r + 1]);
-        double2 cs = cmul(a1, is), cn = cmul(a1, in);
-        double2 j12 = cmul(a1, a2);
-        double hk = h2 * k2[(int64_t)gy * NX + s.ex0 + r];
+        const double2 a1 = a1c[r];
+        const double2 cw = cmul(a2, ia1f[r]), ce = cmul(a2, ia1f[r + 1]);
+        const double2 cs = cmul(a1, is), cn = cmul(a1, in);
+        const double2 j12 = cmul(a1, a2);
+        const double hk = h2 * k2[(int64_t)gy * NX + s.ex0 + r];
         v = mk<T>((R)(-(cw.x + ce.x + cs.x + cn.x) + hk * j12.x), (R)(-(cw.y + ce.y + cs.y + cn.y) + hk * j12.y));
       } else if (r == c + 1) {
-        double2 cw = cmul(a2, ia1f[r]);      // row r couples to column r-1 (west)
+        const double2 cw = cmul(a2, ia1f[r]);      // row r couples to column r-1 (west)
         v = mk<T>((R)cw.x, (R)cw.y);
       } else if (r + 1 == c) {
-        double2 ce = cmul(a2, ia1f[r + 1]);  // row r couples to column r+1 (east)
+        const double2 ce = cmul(a2, ia1f[r + 1]);  // row r couples to column r+1 (east)
         v = mk<T>((R)ce.x, (R)ce.y);
       }
-      if (j > 0) {
-        double2 lr = cmul(a1c[r], is), lc = cmul(a1c[c], is);
-        T l_r = mk<T>((R)lr.x, (R)lr.y), l_c = mk<T>((R)lc.x, (R)lc.y);
-        v = cfms(cmul(l_r, prev[(int64_t)c * ldm + r]), l_c, v);
-      }
+      if (j > 0) v = cfms(cmul(lS[r], prev[(int64_t)c * ldm + r]), lS[c], v);
       W[idx] = v;
     }
-    for (int r = tid; r < m; r += FT) done[r] = 0;
     __syncthreads();
 
     // ---- Gauss-Jordan inversion of W with implicit partial pivoting
     for (int k0 = 0; k0 < m; k0 += PB) {
       const int nb = min(PB, m - k0);
       for (int idx = tid; idx < nb * m; idx += FT) {
-        int t = idx / m, r = idx - t * m;
+        const int t = idx / m, r = idx - t * m;
         P[idx] = W[(int64_t)(k0 + t) * m + r];
       }
       __syncthreads();
+      // 1. eliminate the panel, one thread per row
       for (int t = 0; t < nb; ++t) {
         const int k = k0 + t;
         if (warp == 0) {
           R best = (R)-1;
           int bi = m;
           for (int r = lane; r < m; r += 32) {
-            if (!done[r]) {
-              R v = cabs2(P[t * m + r]);
+            if (mark[r] < 0) {
+              const R v = cabs2(P[t * m + r]);
               if (v > best) { best = v; bi = r; }
             }
           }
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
-            R ob = __shfl_xor_sync(0xffffffffu, best, o);
-            int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            const R ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
           }
+          const int p = bi < m ? bi : 0;
+          T ip = mk<T>(0, 0);
+          if (best > (R)0 && isfinite(best)) ip = cinv(P[t * m + p]);
+          else if (lane == 0) bad = true;
+          // pivot-row values of every panel column after this step (lanes split the columns)
+          for (int tt = lane; tt < nb; tt += 32) X[tt] = tt == t ? ip : cmul(P[tt * m + p], ip);
+          __syncwarp();
           if (lane == 0) {
-            int p = bi < m ? bi : 0;
-            T pv = P[t * m + p];
             piv[k] = p;
             qinv[p] = k;
-            done[p] = 1;
-            if (!(best > (R)0) || !isfinite(best)) {
-              bad = true;
-              IPV[t] = mk<T>(0, 0);
-            } else {
-              IPV[t] = cinv(pv);
-            }
+            mark[p] = k0;
+            IPV[t] = ip;
           }
         }
         __syncthreads();
         const int p = piv[k];
         const T ip = IPV[t];
-        for (int r = tid; r < m; r += FT) F[t * m + r] = P[t * m + r];
-        for (int tt = tid; tt < nb; tt += FT) X[tt] = tt == t ? ip : cmul(P[tt * m + p], ip);
-        __syncthreads();
-        for (int idx = tid; idx < nb * m; idx += FT) {
-          int tt = idx / m, r = idx - tt * m;
-          T nv;
-          if (tt == t) {
-            nv = r == p ? ip : mk<T>(-(F[t * m + r].x * ip.x - F[t * m + r].y * ip.y),
-                                      -(F[t * m + r].x * ip.y + F[t * m + r].y * ip.x));
-          } else {
-            const T x = X[tt];
-            nv = r == p ? x : cfms(F[t * m + r], x, P[idx]);
+        for (int r = tid; r < m; r += FT) {
+          const T f = P[t * m + r];   // multiplier of row r (column k before the step)
+          for (int tt = 0; tt < nb; ++tt) {
+            T nv;
+            if (r == p) nv = X[tt];
+            else if (tt == t) nv = mk<T>(-(f.x * ip.x - f.y * ip.y), -(f.x * ip.y + f.y * ip.x));
+            else nv = cfms(f, X[tt], P[tt * m + r]);
+            P[tt * m + r] = nv;
           }
-          P[idx] = nv;
         }
         __syncthreads();
       }
-      // write the eliminated panel back
+      // 2. write the panel back and gather the pivot rows of the other columns
+      const int ncol = m - nb;
       for (int idx = tid; idx < nb * m; idx += FT) {
-        int t = idx / m, r = idx - t * m;
+        const int t = idx / m, r = idx - t * m;
         W[(int64_t)(k0 + t) * m + r] = P[idx];
       }
-      // apply the panel's nb steps to every other column, one warp per column
-      for (int c = warp; c < m; c += FWARPS) {
-        if (c >= k0 && c < k0 + nb) continue;
-        T col[NPL];
-        T *wc = W + (int64_t)c * m;
+      for (int idx = tid; idx < nb * ncol; idx += FT) {
+        const int t = idx / ncol, cc = idx - t * ncol;
+        const int c = cc < k0 ? cc : cc + nb;
+        Bm[t * m + cc] = W[(int64_t)c * m + piv[k0 + t]];
+      }
+      __syncthreads();
+      // 3. rank-nb update of every other column: C = C(pivot rows zeroed) + panel * Bm
+      const int trow = (m + TR - 1) / TR, tcol = (ncol + TC - 1) / TC;
+      for (int tile = tid; tile < trow * tcol; tile += FT) {
+        const int r0 = (tile % trow) * TR, c0 = (tile / trow) * TC;
+        T acc[TR][TC];
 #pragma unroll
-        for (int e = 0; e < NPL; ++e) {
-          int r = lane + 32 * e;
-          col[e] = r < m ? wc[r] : mk<T>(0, 0);
-        }
-        for (int t = 0; t < nb; ++t) {
-          const int p = piv[k0 + t];
-          const int pe = p >> 5, pl = p & 31;
-          T val = col[0];
+        for (int b = 0; b < TC; ++b) {
+          const int cc = c0 + b;
+          const int c = cc < k0 ? cc : cc + nb;
 #pragma unroll
-          for (int e = 1; e < NPL; ++e)
-            if (pe == e) val = col[e];
-          val.x = __shfl_sync(0xffffffffu, val.x, pl);
-          val.y = __shfl_sync(0xffffffffu, val.y, pl);
-          const T x = cmul(val, IPV[t]);
-#pragma unroll
-          for (int e = 0; e < NPL; ++e) {
-            int r = lane + 32 * e;
-            if (r < m) col[e] = r == p ? x : cfms(F[t * m + r], x, col[e]);
+          for (int a = 0; a < TR; ++a) {
+            const int r = r0 + a;
+            acc[a][b] = (r < m && cc < ncol && mark[r] != k0) ? W[(int64_t)c * m + r] : mk<T>(0, 0);
           }
         }
+        for (int t = 0; t < nb; ++t) {
+          T pa[TR], bb[TC];
 #pragma unroll
-        for (int e = 0; e < NPL; ++e) {
-          int r = lane + 32 * e;
-          if (r < m) wc[r] = col[e];
+          for (int a = 0; a < TR; ++a) pa[a] = r0 + a < m ? P[t * m + r0 + a] : mk<T>(0, 0);
+#pragma unroll
+          for (int b = 0; b < TC; ++b) bb[b] = c0 + b < ncol ? Bm[t * m + c0 + b] : mk<T>(0, 0);
+#pragma unroll
+          for (int a = 0; a < TR; ++a)
+#pragma unroll
+            for (int b = 0; b < TC; ++b) acc[a][b] = cfma(pa[a], bb[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int b = 0; b < TC; ++b) {
+          const int cc = c0 + b;
+          if (cc >= ncol) continue;
+          const int c = cc < k0 ? cc : cc + nb;
+#pragma unroll
+          for (int a = 0; a < TR; ++a)
+            if (r0 + a < m) W[(int64_t)c * m + r0 + a] = acc[a][b];
         }
       }
       __syncthreads();
@@ -195,7 +207,7 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
     // ---- write S_j^{-1}[r][c] = W[p_r][q_c] (column-major) as factor row j
     T *slot = Fs + j * slot_elems;
     for (int64_t idx = tid; idx < mm; idx += FT) {
-      int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
+      const int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
       slot[(int64_t)c * ldm + r] = W[(int64_t)qinv[c] * m + piv[r]];
     }
     __syncthreads();
@@ -203,22 +215,15 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
   if (bad) atomicOr(status, ST_ZERO_PIVOT);
 }
 
-template <typename R, int NPL>
-static cudaError_t launch_factor_t(hd_ctx *ctx, void *factor, void *work, cudaStream_t st) {
-  size_t smem = factor_smem_bytes(ctx->prec, ctx->max_m);
-  cudaError_t e = cudaFuncSetAttribute(k_factor<R, NPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_factor<R, NPL><<<ctx->nsub, FT, smem, st>>>(ctx->d_subs, ctx->d_lpool, ctx->d_k2, ctx->NX, ctx->h * ctx->h,
-                                               reinterpret_cast<C<R> *>(factor), reinterpret_cast<C<R> *>(work),
-                                               ctx->d_status);
-  return cudaGetLastError();
-}
-
 template <typename R>
 static cudaError_t launch_factor_r(hd_ctx *ctx, void *factor, void *work, cudaStream_t st) {
-  if (ctx->max_m <= 128) return launch_factor_t<R, 4>(ctx, factor, work, st);
-  if (ctx->max_m <= 192) return launch_factor_t<R, 6>(ctx, factor, work, st);
-  return launch_factor_t<R, 8>(ctx, factor, work, st);
+  const size_t smem = factor_smem_bytes(ctx->prec, ctx->max_m);
+  cudaError_t e = cudaFuncSetAttribute(k_factor<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_factor<R><<<ctx->nsub, FT, smem, st>>>(ctx->d_subs, ctx->d_lpool, ctx->d_k2, ctx->NX, ctx->h * ctx->h,
+                                          reinterpret_cast<C<R> *>(factor), reinterpret_cast<C<R> *>(work),
+                                          ctx->d_status);
+  return cudaGetLastError();
 }
 
 int run_factor(hd_ctx *ctx, void *factor, void *work, cudaStream_t st) {

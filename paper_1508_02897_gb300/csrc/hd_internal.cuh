@@ -19,31 +19,42 @@ template <typename R> using C = typename cplx<R>::type;
 template <typename T> __host__ __device__ __forceinline__ T mk(decltype(T::x) re, decltype(T::x) im) {
   T z; z.x = re; z.y = im; return z;
 }
-template <typename T> __host__ __device__ __forceinline__ T cadd(T a, T b) { return mk<T>(a.x + b.x, a.y + b.y); }
-template <typename T> __host__ __device__ __forceinline__ T csub(T a, T b) { return mk<T>(a.x - b.x, a.y - b.y); }
-template <typename T> __host__ __device__ __forceinline__ T cmul(T a, T b) {
-  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+// Products are written with explicit round-to-nearest intrinsics so the
+// compiler cannot contract them differently in different instantiations:
+// every kernel variant (for example one or several right-hand sides per CTA)
+// then rounds identically and results are bitwise reproducible.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+template <typename T> __device__ __forceinline__ T cadd(T a, T b) { return mk<T>(add_rn(a.x, b.x), add_rn(a.y, b.y)); }
+template <typename T> __device__ __forceinline__ T csub(T a, T b) { return mk<T>(add_rn(a.x, -b.x), add_rn(a.y, -b.y)); }
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+  return mk<T>(fma_rn(a.x, b.x, -mul_rn(a.y, b.y)), fma_rn(a.x, b.y, mul_rn(a.y, b.x)));
 }
 // acc + a*b
-template <typename T> __host__ __device__ __forceinline__ T cfma(T a, T b, T acc) {
-  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
-  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+template <typename T> __device__ __forceinline__ T cfma(T a, T b, T acc) {
+  acc.x = fma_rn(a.x, b.x, acc.x); acc.x = fma_rn(-a.y, b.y, acc.x);
+  acc.y = fma_rn(a.x, b.y, acc.y); acc.y = fma_rn(a.y, b.x, acc.y);
   return acc;
 }
 // acc - a*b
-template <typename T> __host__ __device__ __forceinline__ T cfms(T a, T b, T acc) {
-  acc.x = fma(-a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
-  acc.y = fma(-a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+template <typename T> __device__ __forceinline__ T cfms(T a, T b, T acc) {
+  acc.x = fma_rn(-a.x, b.x, acc.x); acc.x = fma_rn(a.y, b.y, acc.x);
+  acc.y = fma_rn(-a.x, b.y, acc.y); acc.y = fma_rn(-a.y, b.x, acc.y);
   return acc;
 }
 // acc + conj(a)*b
-template <typename T> __host__ __device__ __forceinline__ T cfma_conj(T a, T b, T acc) {
-  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(a.y, b.y, acc.x);
-  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(-a.y, b.x, acc.y);
+template <typename T> __device__ __forceinline__ T cfma_conj(T a, T b, T acc) {
+  acc.x = fma_rn(a.x, b.x, acc.x); acc.x = fma_rn(a.y, b.y, acc.x);
+  acc.y = fma_rn(a.x, b.y, acc.y); acc.y = fma_rn(-a.y, b.x, acc.y);
   return acc;
 }
-template <typename T> __host__ __device__ __forceinline__ T cinv(T a) {
-  auto d = a.x * a.x + a.y * a.y;
+template <typename T> __device__ __forceinline__ T cinv(T a) {
+  auto d = fma_rn(a.x, a.x, mul_rn(a.y, a.y));
   return mk<T>(a.x / d, -a.y / d);
 }
 __host__ __device__ __forceinline__ float2 to_c(double2 z, float2) { return make_float2((float)z.x, (float)z.y); }
@@ -98,7 +109,9 @@ struct hd_ctx {
   hd::AxisDev *d_axx = nullptr, *d_axy = nullptr;
   int32_t *d_nearx = nullptr, *d_neary = nullptr;  // per global index: box column/row nearest
   int32_t *d_status = nullptr;                    // device status word
-  double *host_stat = nullptr;                    // pinned host mirror of small device results
+  cudaStream_t stream = nullptr;                  // set-up stream: the context's tables are freed on it
+  std::vector<double> host_stat = std::vector<double>(8);   // host mirror of small device results
+  std::vector<unsigned char> host_buf;            // per-solve host mirror (grows on demand)
   // factor binding
   void *factor = nullptr;
   bool factored = false;
@@ -127,11 +140,18 @@ int collect_timers(hd_ctx *ctx);
 
 // kernels launchers (return cudaError_t of the launch)
 cudaError_t launch_setup_tables(hd_ctx *ctx, const double *c_dev, cudaStream_t st);
-cudaError_t launch_matvec(hd_ctx *ctx, const double2 *x, double2 *y, cudaStream_t st);
-cudaError_t launch_residual(hd_ctx *ctx, const double2 *b, const double2 *x, double2 *r, cudaStream_t st);
+cudaError_t launch_matvec(hd_ctx *ctx, const double2 *x, int64_t xs, double2 *y, int64_t ys, int nrhs,
+                          cudaStream_t st);
+cudaError_t launch_residual(hd_ctx *ctx, const double2 *b, const double2 *x, double2 *r, int nrhs, cudaStream_t st);
 cudaError_t launch_rhs(hd_ctx *ctx, const double2 *f, double2 *b, cudaStream_t st);
 int run_factor(hd_ctx *ctx, void *factor, void *work, cudaStream_t st);
-int run_apply(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st);
+// z = M r for nrhs vectors (r and z strided by rs and zs complex entries); the
+// staging buffer holds nrhs per-RHS staging vectors of staging_elems entries.
+int run_apply(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs, void *staging,
+              cudaStream_t st);
+size_t krylov_bytes(int64_t n, int restart, int nrhs);
+int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const hd_gmres_opts *o, void *kws,
+                    void *scratch, hd_gmres_stats *stats, cudaStream_t st);
 size_t subst_ring_bytes(const hd_ctx *ctx, int *stages);
 size_t factor_smem_bytes(int prec, int max_m);
 }  // namespace hd

@@ -9,14 +9,21 @@
 // right-hand side g, and the cycle stops once |g_{j+1}| <= rtol ||b||.  The
 // FP64 true residual b - A x decides convergence at the end of each cycle.
 //
+// Several right-hand sides are solved in lockstep (one independent FGMRES per
+// right-hand side; every kernel takes the right-hand side as blockIdx.y or .z or
+// as a thread index): they share each preconditioner launch, whose factor reads
+// are then amortised over the group.  A right-hand side that converges stops
+// updating its Hessenberg/solution while the others go on.
+//
 // Kernels: k_dots (block partial sums of V^H w, w held in registers), k_reduce
 // (fixed-order sum of the partials: deterministic), k_update (w = base + sgn V c,
-// optionally with block partials of ||w||^2), and single-thread kernels for the
-// O(restart) Hessenberg/Givens/triangular work.  The host reads 32 bytes per
-// Arnoldi step to decide whether to stop.
+// optionally with block partials of ||w||^2), and one-thread-per-right-hand-side
+// kernels for the O(restart) Hessenberg/Givens/triangular work.  The host reads
+// 32 bytes per right-hand side and Arnoldi step to decide whether to stop.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <vector>
 
 #include "hd_internal.cuh"
 
@@ -25,7 +32,10 @@ namespace hd {
 constexpr int DT = 256;           // threads per block of the vector kernels
 constexpr int DE = 8;             // elements per thread
 constexpr int DCHUNK = DT * DE;   // elements per block
+constexpr int DFC = 2048;         // elements of w staged per block in k_dots_df (32 KB of shared memory)
 
+// Batched addressing: right-hand side r of a family of vectors starts at
+// base + r * ld_r; vector k of a basis at + k * ldv.
 __device__ __forceinline__ double2 warp_sum(double2 v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -35,12 +45,15 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
   return v;
 }
 
-// partial[k*G + blk] = sum over the block's chunk of conj(V[k][i]) w[i], k < nk.
-__global__ void __launch_bounds__(DT) k_dots(const double2 *__restrict__ V, int64_t ldv, int nk,
-                                             const double2 *__restrict__ w, int64_t n,
-                                             double2 *__restrict__ partial, int G) {
+// partial[r][k][blk] = sum over the block's chunk of conj(V_r[k][i]) w_r[i], k < nk.
+__global__ void __launch_bounds__(DT) k_dots(const double2 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
+                                             const double2 *__restrict__ w_all, int64_t ldw, int64_t n,
+                                             double2 *__restrict__ partial_all, int G, int64_t ldp) {
   extern __shared__ double2 red[];  // [DT/32][nk]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double2 *w = w_all + (int64_t)blockIdx.y * ldw;
+  const double2 *Vr = V + (int64_t)blockIdx.y * ldvr;
+  double2 *partial = partial_all + (int64_t)blockIdx.y * ldp;
   const int64_t base = (int64_t)blockIdx.x * DCHUNK + tid;
   double2 wv[DE];
 #pragma unroll
@@ -49,7 +62,7 @@ __global__ void __launch_bounds__(DT) k_dots(const double2 *__restrict__ V, int6
     wv[e] = i < n ? w[i] : make_double2(0.0, 0.0);
   }
   for (int k = 0; k < nk; ++k) {
-    const double2 *vk = V + (int64_t)k * ldv;
+    const double2 *vk = Vr + (int64_t)k * ldv;
     double2 acc = make_double2(0.0, 0.0);
 #pragma unroll
     for (int e = 0; e < DE; ++e) {
@@ -67,37 +80,46 @@ __global__ void __launch_bounds__(DT) k_dots(const double2 *__restrict__ V, int6
   }
 }
 
-// out[k] = sum_b partial[k*G + b] in a fixed order.
-__global__ void __launch_bounds__(256) k_reduce(const double2 *__restrict__ partial, int G, double2 *__restrict__ out) {
+// out[r*ldo + k] = sum_b partial[r][k][b] in a fixed order; grid (nk, nrhs).
+__global__ void __launch_bounds__(256) k_reduce(const double2 *__restrict__ partial, int G, int64_t ldp,
+                                                double2 *__restrict__ out, int ldo) {
   __shared__ double2 sm[256];
   const int k = blockIdx.x, tid = threadIdx.x;
+  const double2 *p = partial + (int64_t)blockIdx.y * ldp + (int64_t)k * G;
   double2 acc = make_double2(0.0, 0.0);
-  for (int b = tid; b < G; b += 256) acc = cadd(acc, partial[(int64_t)k * G + b]);
+  for (int b = tid; b < G; b += 256) acc = cadd(acc, p[b]);
   sm[tid] = acc;
   __syncthreads();
   for (int s = 128; s > 0; s >>= 1) {
     if (tid < s) sm[tid] = cadd(sm[tid], sm[tid + s]);
     __syncthreads();
   }
-  if (tid == 0) out[k] = sm[0];
+  if (tid == 0) out[(int64_t)blockIdx.y * ldo + k] = sm[0];
 }
 
-// y = base + sgn * sum_k V[k] coef[k]; optionally normpart[blk] = block sum of |y|^2.
+// y_r = base_r + sgn * sum_{k < nk_r} V_r[k] coef_r[k]; optionally normpart[r][blk] =
+// block sum of |y_r|^2.  nk_r = nk_per[r] when nk_per is given, else nk.
 template <bool NORM>
-__global__ void __launch_bounds__(DT) k_update(const double2 *__restrict__ V, int64_t ldv, int nk,
-                                               const double2 *__restrict__ coef, double sgn, const double2 *base,
-                                               double2 *y, int64_t n, double2 *__restrict__ normpart) {
+__global__ void __launch_bounds__(DT) k_update(const double2 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
+                                               const int *__restrict__ nk_per, const double2 *__restrict__ coef_all,
+                                               int ldc, double sgn, const double2 *base_all, double2 *y_all, int64_t ldy,
+                                               int64_t n, double2 *__restrict__ normpart_all, int64_t ldp) {
   extern __shared__ double2 cs[];  // [nk]
   __shared__ double nsm[DT / 32];
-  const int tid = threadIdx.x;
-  for (int k = tid; k < nk; k += DT) cs[k] = coef[k];
+  const int tid = threadIdx.x, r = blockIdx.y;
+  const int nkr = nk_per ? nk_per[r] : nk;
+  const double2 *coef = coef_all + (int64_t)r * ldc;
+  const double2 *Vr = V + (int64_t)r * ldvr;
+  const double2 *base = base_all + (int64_t)r * ldy;
+  double2 *y = y_all + (int64_t)r * ldy;
+  for (int k = tid; k < nkr; k += DT) cs[k] = coef[k];
   __syncthreads();
   const int64_t b0 = (int64_t)blockIdx.x * DCHUNK + tid;
   double2 acc[DE];
 #pragma unroll
   for (int e = 0; e < DE; ++e) acc[e] = make_double2(0.0, 0.0);
-  for (int k = 0; k < nk; ++k) {
-    const double2 *vk = V + (int64_t)k * ldv;
+  for (int k = 0; k < nkr; ++k) {
+    const double2 *vk = Vr + (int64_t)k * ldv;
     const double2 ck = cs[k];
 #pragma unroll
     for (int e = 0; e < DE; ++e) {
@@ -110,7 +132,7 @@ __global__ void __launch_bounds__(DT) k_update(const double2 *__restrict__ V, in
   for (int e = 0; e < DE; ++e) {
     int64_t i = b0 + (int64_t)DT * e;
     if (i < n) {
-      double2 bv = base ? base[i] : make_double2(0.0, 0.0);
+      double2 bv = base[i];
       double2 o = make_double2(bv.x + sgn * acc[e].x, bv.y + sgn * acc[e].y);
       y[i] = o;
       if (NORM) nrm += o.x * o.x + o.y * o.y;
@@ -124,20 +146,22 @@ __global__ void __launch_bounds__(DT) k_update(const double2 *__restrict__ V, in
     if (tid == 0) {
       double s = 0.0;
       for (int q = 0; q < DT / 32; ++q) s += nsm[q];
-      normpart[blockIdx.x] = make_double2(s, 0.0);
+      normpart_all[(int64_t)r * ldp + blockIdx.x] = make_double2(s, 0.0);
     }
   }
 }
 
-// v = w * (1/scale) with scale = sqrt(red->x) (a squared norm) or the host value.
-__global__ void __launch_bounds__(256) k_scale(const double2 *__restrict__ w, const double2 *__restrict__ red,
-                                               double host_scale, double2 *__restrict__ v, int64_t n) {
+// v_r = w_r / sqrt(red[4 r].x) (a squared norm); grid (.., nrhs).
+__global__ void __launch_bounds__(256) k_scale(const double2 *__restrict__ w_all, int64_t ldw,
+                                               const double2 *__restrict__ red, double2 *__restrict__ v_all,
+                                               int64_t ldvr, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = red ? sqrt(red->x) : host_scale;
+  const int r = blockIdx.y;
+  double s = sqrt(red[4 * r].x);
   double inv = s > 0.0 ? 1.0 / s : 0.0;
-  double2 a = w[i];
-  v[i] = make_double2(a.x * inv, a.y * inv);
+  double2 a = w_all[(int64_t)r * ldw + i];
+  v_all[(int64_t)r * ldvr + i] = make_double2(a.x * inv, a.y * inv);
 }
 
 // ---------------------------------------------------------------- double-single Arnoldi
@@ -147,8 +171,6 @@ __global__ void __launch_bounds__(256) k_scale(const double2 *__restrict__ w, co
 // and updates use double-single arithmetic (Dekker/Knuth error-free products
 // and sums on the FP32 pipes).  The FP64 copy of the newest basis vector feeds
 // the preconditioner; the residuals, norms, Hessenberg and Givens work stay FP64.
-constexpr int DFC = 4096;  // elements of w staged per block in k_dots_df
-
 __device__ __forceinline__ float2 split_d(double x) {
   float h = __double2float_rn(x);
   float l = __double2float_rn(x - (double)h);
@@ -182,14 +204,17 @@ __device__ __forceinline__ void ds_add(float &sh, float &sl, float bh, float bl)
   ds_renorm(sh, sl);
 }
 
-// partial[k*G + blk] = sum over the block's DFC elements of conj(V[k][i]) w[i].
-__global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, int64_t ldv, int nk,
-                                                 const double2 *__restrict__ w, int64_t n,
-                                                 double2 *__restrict__ partial, int G) {
+// partial[r][k][blk] = sum over the block's DFC elements of conj(V_r[k][i]) w_r[i].
+__global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
+                                                 const double2 *__restrict__ w_all, int64_t ldw, int64_t n,
+                                                 double2 *__restrict__ partial_all, int G, int64_t ldp) {
   extern __shared__ float4 wsm[];  // [DFC]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t base = (int64_t)blockIdx.x * DFC;
   const int cnt = (int)min((int64_t)DFC, n - base);
+  const double2 *w = w_all + (int64_t)blockIdx.y * ldw;
+  const float4 *Vr = V + (int64_t)blockIdx.y * ldvr;
+  double2 *partial = partial_all + (int64_t)blockIdx.y * ldp;
   for (int i = tid; i < DFC; i += 256) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < cnt) {
@@ -201,7 +226,7 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, i
   }
   __syncthreads();
   for (int k = warp; k < nk; k += 8) {
-    const float4 *vk = V + (int64_t)k * ldv + base;
+    const float4 *vk = Vr + (int64_t)k * ldv + base;
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
     for (int i0 = 0; i0 < cnt; i0 += 256) {
       float4 vv[8];
@@ -232,19 +257,24 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, i
   }
 }
 
-// y = base - sum_k V[k] coef[k] (double-single accumulation, FP64 result);
-// optionally normpart[blk] = block sum of |y|^2.
+// y_r = base_r - sum_k V_r[k] coef_r[k] (double-single accumulation, FP64 result);
+// optionally normpart[r][blk] = block sum of |y_r|^2.
 template <bool NORM>
-__global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, int64_t ldv, int nk,
-                                                  const double2 *__restrict__ coef, const double2 *base, double2 *y,
-                                                  int64_t n, double2 *__restrict__ normpart) {
+__global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
+                                                  const double2 *__restrict__ coef_all, int ldc, const double2 *base_all,
+                                                  double2 *y_all, int64_t ldy, int64_t n,
+                                                  double2 *__restrict__ normpart_all, int64_t ldp) {
   extern __shared__ float4 csm[];  // [nk]
   __shared__ double nsm[DT / 32];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, r = blockIdx.y;
+  const double2 *coef = coef_all + (int64_t)r * ldc;
+  const float4 *Vr = V + (int64_t)r * ldvr;
+  const double2 *base = base_all + (int64_t)r * ldy;
+  double2 *y = y_all + (int64_t)r * ldy;
   for (int k = tid; k < nk; k += DT) {
     double2 c = coef[k];
-    float2 r = split_d(c.x), m = split_d(c.y);
-    csm[k] = make_float4(r.x, r.y, m.x, m.y);
+    float2 cr = split_d(c.x), ci = split_d(c.y);
+    csm[k] = make_float4(cr.x, cr.y, ci.x, ci.y);
   }
   __syncthreads();
   constexpr int E = 4;
@@ -257,7 +287,7 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
     for (int e = 0; e < E; ++e) { rh[e] = rl[e] = ih[e] = il[e] = 0.f; }
     for (int k = 0; k < nk; ++k) {
       const float4 c = csm[k];
-      const float4 *vk = V + (int64_t)k * ldv;
+      const float4 *vk = Vr + (int64_t)k * ldv;
       float4 a[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
@@ -295,57 +325,67 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
     if (tid == 0) {
       double s = 0.0;
       for (int q = 0; q < DT / 32; ++q) s += nsm[q];
-      normpart[blockIdx.x] = make_double2(s, 0.0);
+      normpart_all[(int64_t)r * ldp + blockIdx.x] = make_double2(s, 0.0);
     }
   }
 }
 
-// v = w / scale written twice: split into V (double-single) and FP64 into vin.
-__global__ void __launch_bounds__(256) k_scale_df(const double2 *__restrict__ w, const double2 *__restrict__ red,
-                                                  double host_scale, float4 *__restrict__ vout,
-                                                  double2 *__restrict__ vin, int64_t n) {
+// v_r = w_r / sqrt(red[4 r].x) written twice: split into V (double-single) and FP64 into vin.
+__global__ void __launch_bounds__(256) k_scale_df(const double2 *__restrict__ w_all, int64_t ldw,
+                                                  const double2 *__restrict__ red, float4 *__restrict__ vout_all,
+                                                  int64_t ldvr, double2 *__restrict__ vin_all, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = red ? sqrt(red->x) : host_scale;
+  const int r = blockIdx.y;
+  double s = sqrt(red[4 * r].x);
   double inv = s > 0.0 ? 1.0 / s : 0.0;
-  double2 a = w[i];
+  double2 a = w_all[(int64_t)r * ldw + i];
   double2 v = make_double2(a.x * inv, a.y * inv);
-  float2 r = split_d(v.x), m = split_d(v.y);
-  vout[i] = make_float4(r.x, r.y, m.x, m.y);
-  vin[i] = v;
+  float2 cr = split_d(v.x), ci = split_d(v.y);
+  vout_all[(int64_t)r * ldvr + i] = make_float4(cr.x, cr.y, ci.x, ci.y);
+  vin_all[(int64_t)r * n + i] = v;
 }
 
+// ---------------------------------------------------------------- small per-RHS work
 struct GmresDev {
-  double2 *H;    // [restart][ldh] column-major Hessenberg
-  double *cs;    // [restart]
-  double2 *sn;   // [restart]
-  double2 *g;    // [restart+1]
-  double2 *y;    // [restart]
-  double2 *h1, *h2;  // [restart+1]
-  double2 *red;      // [4]
-  double *stat;      // [4] host-visible summary
-  int ldh;
+  double2 *H;        // [nrhs][restart][ldh] column-major Hessenberg per right-hand side
+  double *cs;        // [nrhs][restart]
+  double2 *sn;       // [nrhs][restart]
+  double2 *g;        // [nrhs][ldh]
+  double2 *y;        // [nrhs][restart]
+  double2 *h1, *h2;  // [nrhs][ldh]
+  double2 *red;      // [nrhs][4]
+  double *stat;      // [nrhs][4] host-visible summary: |g_{j+1}|, h_{j+1,j}, non-finite flag
+  int *live;         // [nrhs] 1 while the right-hand side takes Arnoldi steps
+  int *kcnt;         // [nrhs] Arnoldi steps of the current cycle
+  int ldh, restart, nrhs;
 };
 
 __device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, a.y); }
 
-__global__ void k_cycle_init(GmresDev d, double beta) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    for (int i = 0; i < d.ldh; ++i) d.g[i] = make_double2(0.0, 0.0);
-    d.g[0] = make_double2(beta, 0.0);
-  }
+__global__ void k_cycle_init(GmresDev d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrhs || !d.live[r]) return;
+  double2 *g = d.g + (int64_t)r * d.ldh;
+  for (int i = 0; i < d.ldh; ++i) g[i] = make_double2(0.0, 0.0);
+  g[0] = make_double2(sqrt(d.red[4 * r].x), 0.0);
 }
 
 // Column j of H from the two CGS passes, old rotations, new rotation, g update.
 __global__ void k_arnoldi_step(GmresDev d, int j) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double2 *Hj = d.H + (int64_t)j * d.ldh;
-  for (int i = 0; i <= j; ++i) Hj[i] = cadd(d.h1[i], d.h2[i]);
-  double hn = sqrt(d.red[0].x);
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrhs || !d.live[r]) return;
+  double2 *Hj = d.H + ((int64_t)r * d.restart + j) * d.ldh;
+  const double2 *h1 = d.h1 + (int64_t)r * d.ldh, *h2 = d.h2 + (int64_t)r * d.ldh;
+  double *cs = d.cs + (int64_t)r * d.restart;
+  double2 *sn = d.sn + (int64_t)r * d.restart;
+  double2 *g = d.g + (int64_t)r * d.ldh;
+  for (int i = 0; i <= j; ++i) Hj[i] = cadd(h1[i], h2[i]);
+  double hn = sqrt(d.red[4 * r].x);
   Hj[j + 1] = make_double2(hn, 0.0);
   for (int i = 0; i < j; ++i) {
-    double c = d.cs[i];
-    double2 s = d.sn[i];
+    double c = cs[i];
+    double2 s = sn[i];
     double2 a = Hj[i], b = Hj[i + 1];
     double2 t0 = make_double2(c * a.x, c * a.y);
     t0 = cfma(s, b, t0);
@@ -368,28 +408,33 @@ __global__ void k_arnoldi_step(GmresDev d, int j) {
     double2 ph = make_double2(a.x / aa, a.y / aa);
     s = cmul(ph, make_double2(b.x / t, -b.y / t));
   }
-  d.cs[j] = c;
-  d.sn[j] = s;
+  cs[j] = c;
+  sn[j] = s;
   double2 nj = make_double2(c * a.x, c * a.y);
   Hj[j] = cfma(s, b, nj);
   Hj[j + 1] = make_double2(0.0, 0.0);
-  double2 gj = d.g[j];
+  double2 gj = g[j];
   double2 sc = make_double2(-s.x, s.y);
-  d.g[j + 1] = cmul(sc, gj);
-  d.g[j] = make_double2(c * gj.x, c * gj.y);
-  d.stat[0] = cabs_(d.g[j + 1]);
-  d.stat[1] = hn;
-  d.stat[2] = (isfinite(hn) && isfinite(d.stat[0])) ? 0.0 : 1.0;
+  g[j + 1] = cmul(sc, gj);
+  g[j] = make_double2(c * gj.x, c * gj.y);
+  double *stat = d.stat + 4 * r;
+  stat[0] = cabs_(g[j + 1]);
+  stat[1] = hn;
+  stat[2] = (isfinite(hn) && isfinite(stat[0])) ? 0.0 : 1.0;
 }
 
-// y = H[0:k,0:k]^{-1} g[0:k] (upper triangular).
-__global__ void k_trisolve(GmresDev d, int k) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// y_r = H_r[0:k,0:k]^{-1} g_r[0:k] (upper triangular), k = kcnt[r].
+__global__ void k_trisolve(GmresDev d) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrhs) return;
+  const int k = d.kcnt[r];
+  const double2 *H = d.H + (int64_t)r * d.restart * d.ldh;
+  const double2 *g = d.g + (int64_t)r * d.ldh;
+  double2 *y = d.y + (int64_t)r * d.restart;
   for (int i = k - 1; i >= 0; --i) {
-    double2 acc = d.g[i];
-    for (int l = i + 1; l < k; ++l) acc = cfms(d.H[(int64_t)l * d.ldh + i], d.y[l], acc);
-    double2 hii = d.H[(int64_t)i * d.ldh + i];
-    d.y[i] = cmul(acc, cinv(hii));
+    double2 acc = g[i];
+    for (int l = i + 1; l < k; ++l) acc = cfms(H[(int64_t)l * d.ldh + i], y[l], acc);
+    y[i] = cmul(acc, cinv(H[(int64_t)i * d.ldh + i]));
   }
 }
 
@@ -398,211 +443,256 @@ static size_t al(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct KrylovLayout {
   int64_t n;
-  int restart, G, Gdf;
-  size_t off_V, off_Z, off_w, off_vin, off_part, off_h1, off_h2, off_red, off_H, off_cs, off_sn, off_g, off_y, off_stat, total;
+  int restart, nrhs, G, Gdf, Gmax;
+  size_t off_V, off_Z, off_w, off_vin, off_part, off_h1, off_h2, off_red, off_H, off_cs, off_sn, off_g, off_y,
+      off_stat, off_live, total;
 };
 
-static KrylovLayout krylov_layout(int64_t n, int restart) {
+static KrylovLayout krylov_layout(int64_t n, int restart, int nrhs) {
   KrylovLayout L;
-  L.n = n; L.restart = restart;
+  L.n = n; L.restart = restart; L.nrhs = nrhs;
   L.G = (int)((n + DCHUNK - 1) / DCHUNK);
   L.Gdf = (int)((n + DFC - 1) / DFC);
-  size_t o = 0, c16 = sizeof(double2);
-  L.off_V = o; o += al(c16 * n * (restart + 1));
-  L.off_Z = o; o += al(c16 * n * restart);
-  L.off_w = o; o += al(c16 * n);
-  L.off_vin = o; o += al(c16 * n);
-  L.off_part = o; o += al(c16 * (size_t)std::max(L.G, L.Gdf) * (restart + 1));
-  L.off_h1 = o; o += al(c16 * (restart + 1));
-  L.off_h2 = o; o += al(c16 * (restart + 1));
-  L.off_red = o; o += al(c16 * 4);
-  L.off_H = o; o += al(c16 * (size_t)(restart + 1) * restart);
-  L.off_cs = o; o += al(sizeof(double) * restart);
-  L.off_sn = o; o += al(c16 * restart);
-  L.off_g = o; o += al(c16 * (restart + 1));
-  L.off_y = o; o += al(c16 * restart);
-  L.off_stat = o; o += al(sizeof(double) * 4);
+  L.Gmax = std::max(L.G, L.Gdf);
+  const size_t c16 = sizeof(double2), B = (size_t)nrhs, R = (size_t)restart;
+  size_t o = 0;
+  L.off_V = o; o += al(c16 * n * (R + 1) * B);
+  L.off_Z = o; o += al(c16 * n * R * B);
+  L.off_w = o; o += al(c16 * n * B);
+  L.off_vin = o; o += al(c16 * n * B);
+  L.off_part = o; o += al(c16 * (size_t)L.Gmax * (R + 1) * B);
+  L.off_h1 = o; o += al(c16 * (R + 1) * B);
+  L.off_h2 = o; o += al(c16 * (R + 1) * B);
+  L.off_red = o; o += al(c16 * 4 * B);
+  L.off_H = o; o += al(c16 * (R + 1) * R * B);
+  L.off_cs = o; o += al(sizeof(double) * R * B);
+  L.off_sn = o; o += al(c16 * R * B);
+  L.off_g = o; o += al(c16 * (R + 1) * B);
+  L.off_y = o; o += al(c16 * R * B);
+  L.off_stat = o; o += al(sizeof(double) * 4 * B);
+  L.off_live = o; o += al(sizeof(int) * 2 * B);   // live [B] followed by kcnt [B]
   L.total = o;
   return L;
 }
 
-size_t krylov_bytes(int64_t n, int restart) { return krylov_layout(n, restart).total; }
+size_t krylov_bytes(int64_t n, int restart, int nrhs) { return krylov_layout(n, restart, nrhs).total; }
 
 // ---------------------------------------------------------------- driver
-struct Vec {
+#define KCHK(x)                                      \
+  do {                                               \
+    cudaError_t e_ = (x);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
+  } while (0)
+
+struct Krylov {
   hd_ctx *ctx;
   cudaStream_t st;
   KrylovLayout L;
   char *ws;
-  double2 *V() const { return reinterpret_cast<double2 *>(ws + L.off_V); }
-  double2 *Z() const { return reinterpret_cast<double2 *>(ws + L.off_Z); }
-  double2 *w() const { return reinterpret_cast<double2 *>(ws + L.off_w); }
-  double2 *part() const { return reinterpret_cast<double2 *>(ws + L.off_part); }
-  double2 *vin() const { return reinterpret_cast<double2 *>(ws + L.off_vin); }
-  float4 *Vdf() const { return reinterpret_cast<float4 *>(ws + L.off_V); }
+  int B;
+  template <typename T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+  double2 *V() const { return at<double2>(L.off_V); }
+  float4 *Vdf() const { return at<float4>(L.off_V); }
+  double2 *Z() const { return at<double2>(L.off_Z); }
+  double2 *w() const { return at<double2>(L.off_w); }
+  double2 *vin() const { return at<double2>(L.off_vin); }
+  double2 *part() const { return at<double2>(L.off_part); }
+  int64_t ldvr() const { return L.n * (L.restart + 1); }
+  int64_t ldp() const { return (int64_t)L.Gmax * (L.restart + 1); }
 
-  cudaError_t dots_df(int nk, const double2 *x, double2 *out) {
+  // out[r*ldo + k] = V_r[k]^H x_r, k < nk (V given with its per-RHS stride)
+  cudaError_t dots(const double2 *Vb, int64_t vr, int nk, const double2 *x, double2 *out, int ldo) {
     tic(ctx, T_ARNOLDI, st);
-    k_dots_df<<<L.Gdf, 256, sizeof(float4) * DFC, st>>>(Vdf(), L.n, nk, x, L.n, part(), L.Gdf);
-    k_reduce<<<nk, 256, 0, st>>>(part(), L.Gdf, out);
+    k_dots<<<dim3(L.G, B), DT, sizeof(double2) * (DT / 32) * nk, st>>>(Vb, L.n, vr, nk, x, L.n, L.n, part(), L.G, ldp());
+    k_reduce<<<dim3(nk, B), 256, 0, st>>>(part(), L.G, ldp(), out, ldo);
     toc(ctx, T_ARNOLDI, st, 2);
     return cudaGetLastError();
   }
-  cudaError_t update_df(int nk, const double2 *coef, double2 *w, double2 *norm_out) {
+  cudaError_t update(const double2 *Vb, int64_t vr, int nk, const int *nk_per, const double2 *coef, int ldc,
+                     double sgn, const double2 *base, double2 *y, double2 *norm_out) {
     tic(ctx, T_ARNOLDI, st);
-    size_t sm = sizeof(float4) * nk;
+    size_t sm = sizeof(double2) * std::max(nk, 1);
     if (norm_out) {
-      k_update_df<true><<<L.G, DT, sm, st>>>(Vdf(), L.n, nk, coef, w, w, L.n, part());
-      k_reduce<<<1, 256, 0, st>>>(part(), L.G, norm_out);
+      k_update<true><<<dim3(L.G, B), DT, sm, st>>>(Vb, L.n, vr, nk, nk_per, coef, ldc, sgn, base, y, L.n, L.n, part(), ldp());
+      k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4);
     } else {
-      k_update_df<false><<<L.G, DT, sm, st>>>(Vdf(), L.n, nk, coef, w, w, L.n, nullptr);
+      k_update<false><<<dim3(L.G, B), DT, sm, st>>>(Vb, L.n, vr, nk, nk_per, coef, ldc, sgn, base, y, L.n, L.n, nullptr, 0);
     }
     toc(ctx, T_ARNOLDI, st, norm_out ? 2 : 1);
     return cudaGetLastError();
   }
-
-  cudaError_t dots(const double2 *Vb, int nk, const double2 *x, double2 *out) {
+  cudaError_t dots_df(int nk, const double2 *x, double2 *out, int ldo) {
     tic(ctx, T_ARNOLDI, st);
-    k_dots<<<L.G, DT, sizeof(double2) * (DT / 32) * nk, st>>>(Vb, L.n, nk, x, L.n, part(), L.G);
-    k_reduce<<<nk, 256, 0, st>>>(part(), L.G, out);
+    k_dots_df<<<dim3(L.Gdf, B), 256, sizeof(float4) * DFC, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp());
+    k_reduce<<<dim3(nk, B), 256, 0, st>>>(part(), L.Gdf, ldp(), out, ldo);
     toc(ctx, T_ARNOLDI, st, 2);
     return cudaGetLastError();
   }
-  cudaError_t update(const double2 *Vb, int nk, const double2 *coef, double sgn, const double2 *base, double2 *y,
-                     double2 *norm_out) {
+  cudaError_t update_df(int nk, const double2 *coef, int ldc, double2 *wv, double2 *norm_out) {
     tic(ctx, T_ARNOLDI, st);
-    size_t sm = sizeof(double2) * nk;
+    size_t sm = sizeof(float4) * nk;
     if (norm_out) {
-      k_update<true><<<L.G, DT, sm, st>>>(Vb, L.n, nk, coef, sgn, base, y, L.n, part());
-      k_reduce<<<1, 256, 0, st>>>(part(), L.G, norm_out);
+      k_update_df<true><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, wv, wv, L.n, L.n, part(), ldp());
+      k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4);
     } else {
-      k_update<false><<<L.G, DT, sm, st>>>(Vb, L.n, nk, coef, sgn, base, y, L.n, nullptr);
+      k_update_df<false><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, wv, wv, L.n, L.n, nullptr, 0);
     }
     toc(ctx, T_ARNOLDI, st, norm_out ? 2 : 1);
     return cudaGetLastError();
   }
 };
 
-#define KCHK(x)                                   \
-  do {                                            \
-    cudaError_t e_ = (x);                         \
-    if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
-  } while (0)
-
-int run_gmres_one(hd_ctx *ctx, const double2 *b, double2 *x, const hd_gmres_opts *o, void *kws, void *scratch,
-                  hd_gmres_stats *stats, double *host_stat, cudaStream_t st) {
+int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int B, const hd_gmres_opts *o, void *kws,
+                    void *scratch, hd_gmres_stats *stats, cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
   const int64_t n = (int64_t)ctx->NX * ctx->NY;
   const int R = o->restart;
-  Vec v{ctx, st, krylov_layout(n, R), reinterpret_cast<char *>(kws)};
+  Krylov K{ctx, st, krylov_layout(n, R, B), reinterpret_cast<char *>(kws), B};
   GmresDev d;
-  char *ws = v.ws;
-  d.H = reinterpret_cast<double2 *>(ws + v.L.off_H);
-  d.cs = reinterpret_cast<double *>(ws + v.L.off_cs);
-  d.sn = reinterpret_cast<double2 *>(ws + v.L.off_sn);
-  d.g = reinterpret_cast<double2 *>(ws + v.L.off_g);
-  d.y = reinterpret_cast<double2 *>(ws + v.L.off_y);
-  d.h1 = reinterpret_cast<double2 *>(ws + v.L.off_h1);
-  d.h2 = reinterpret_cast<double2 *>(ws + v.L.off_h2);
-  d.red = reinterpret_cast<double2 *>(ws + v.L.off_red);
-  d.stat = reinterpret_cast<double *>(ws + v.L.off_stat);
-  d.ldh = R + 1;
-  const unsigned gs = (unsigned)((n + 255) / 256);
+  d.H = K.at<double2>(K.L.off_H);
+  d.cs = K.at<double>(K.L.off_cs);
+  d.sn = K.at<double2>(K.L.off_sn);
+  d.g = K.at<double2>(K.L.off_g);
+  d.y = K.at<double2>(K.L.off_y);
+  d.h1 = K.at<double2>(K.L.off_h1);
+  d.h2 = K.at<double2>(K.L.off_h2);
+  d.red = K.at<double2>(K.L.off_red);
+  d.stat = K.at<double>(K.L.off_stat);
+  d.live = K.at<int>(K.L.off_live);
+  d.kcnt = d.live + B;
+  d.ldh = R + 1; d.restart = R; d.nrhs = B;
   const bool dsm = o->arnoldi == HD_ARNOLDI_DS;
   if (dsm) KCHK(cudaFuncSetAttribute(k_dots_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float4) * DFC)));
+  const dim3 gs((unsigned)((n + 255) / 256), B);
+  const unsigned tb = (unsigned)std::min(B, 256), nb = (unsigned)((B + 255) / 256);
 
-  auto read_red = [&](double *out) -> int {
-    KCHK(cudaMemcpyAsync(host_stat, d.red, sizeof(double2), cudaMemcpyDeviceToHost, st));
+  // host mirror: stat [B][4] doubles | red [B][4] complex | live [B] | kcnt [B]
+  const size_t hb = sizeof(double) * 4 * B + sizeof(double2) * 4 * B + 2 * sizeof(int) * B;
+  if (ctx->host_buf.size() < hb) ctx->host_buf.resize(hb);
+  double *h_stat = reinterpret_cast<double *>(ctx->host_buf.data());
+  double2 *h_red = reinterpret_cast<double2 *>(h_stat + 4 * B);
+  int *h_live = reinterpret_cast<int *>(h_red + 4 * B);
+  int *h_kcnt = h_live + B;
+
+  auto read_red = [&]() -> int {
+    KCHK(cudaMemcpyAsync(h_red, d.red, sizeof(double2) * 4 * B, cudaMemcpyDeviceToHost, st));
     KCHK(cudaStreamSynchronize(st));
-    *out = host_stat[0];
     return HD_OK;
   };
+  auto push_masks = [&]() -> int {
+    KCHK(cudaMemcpyAsync(d.live, h_live, sizeof(int) * 2 * B, cudaMemcpyHostToDevice, st));  // live and kcnt are adjacent
+    return HD_OK;
+  };
+  static_assert(sizeof(int) == 4, "int layout");
 
-  // ||b||
-  KCHK(v.dots(b, 1, b, d.red));
-  double bn2;
-  int rc = read_red(&bn2);
+  // ||b_r||
+  KCHK(K.dots(b, n, 1, b, d.red, 4));
+  int rc = read_red();
   if (rc) return rc;
-  const double bnorm = std::sqrt(bn2);
-  stats->iters = 0; stats->restarts = 0; stats->converged = 0; stats->status = HD_OK;
-  stats->relres_est = 1.0; stats->relres_true = 1.0;
-  if (!o->use_x0) KCHK(cudaMemsetAsync(x, 0, sizeof(double2) * n, st));
-  if (!(bnorm > 0.0)) {
-    if (!o->use_x0) {
-      stats->converged = 1; stats->relres_est = 0; stats->relres_true = 0;
-      return HD_OK;
-    }
-  }
-  int iters = 0, cycles = 0;
+  std::vector<double> bnorm(B), rel_est(B, 1.0), rel_true(B, 1.0);
+  std::vector<int> iters(B, 0), done(B, 0), conv(B, 0), status(B, HD_OK);
+  for (int r = 0; r < B; ++r) bnorm[r] = std::sqrt(h_red[4 * r].x);
+  if (!o->use_x0) KCHK(cudaMemsetAsync(x, 0, sizeof(double2) * n * B, st));
+  int cycles = 0;
   for (;;) {
     // true residual r = b - A x (or b itself for x0 = 0 on the first cycle)
     if (o->use_x0 || cycles > 0) {
       tic(ctx, T_MATVEC, st);
-      KCHK(launch_residual(ctx, b, x, v.w(), st));
+      KCHK(launch_residual(ctx, b, x, K.w(), B, st));
       toc(ctx, T_MATVEC, st, 1);
     } else {
-      KCHK(cudaMemcpyAsync(v.w(), b, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+      KCHK(cudaMemcpyAsync(K.w(), b, sizeof(double2) * n * B, cudaMemcpyDeviceToDevice, st));
     }
-    KCHK(v.dots(v.w(), 1, v.w(), d.red));
-    double rn2;
-    rc = read_red(&rn2);
+    KCHK(K.dots(K.w(), n, 1, K.w(), d.red, 4));
+    rc = read_red();
     if (rc) return rc;
-    const double beta = std::sqrt(rn2);
-    stats->relres_true = bnorm > 0 ? beta / bnorm : 0.0;
-    if (!std::isfinite(beta)) { stats->status = HD_ERR_NUMERIC; return HD_ERR_NUMERIC; }
-    if (stats->relres_true <= o->rtol) { stats->converged = 1; break; }
-    if (iters >= o->max_iters) break;
+    bool any = false;
+    for (int r = 0; r < B; ++r) {
+      if (done[r]) { h_live[r] = 0; h_kcnt[r] = 0; continue; }
+      const double beta = std::sqrt(h_red[4 * r].x);
+      rel_true[r] = bnorm[r] > 0 ? beta / bnorm[r] : 0.0;
+      if (!std::isfinite(beta)) { status[r] = HD_ERR_NUMERIC; done[r] = 1; }
+      else if (rel_true[r] <= o->rtol) { conv[r] = 1; done[r] = 1; }
+      else if (iters[r] >= o->max_iters) { done[r] = 1; }
+      h_live[r] = !done[r];
+      h_kcnt[r] = 0;
+      any = any || !done[r];
+    }
+    if (!any) break;
+    if ((rc = push_masks())) return rc;
     tic(ctx, T_ARNOLDI, st);
-    k_cycle_init<<<1, 1, 0, st>>>(d, beta);
-    if (dsm) k_scale_df<<<gs, 256, 0, st>>>(v.w(), nullptr, beta, v.Vdf(), v.vin(), n);
-    else k_scale<<<gs, 256, 0, st>>>(v.w(), nullptr, beta, v.V(), n);
+    k_cycle_init<<<nb, tb, 0, st>>>(d);
+    if (dsm) k_scale_df<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.Vdf(), K.ldvr(), K.vin(), n);
+    else k_scale<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.V(), K.ldvr(), n);
     toc(ctx, T_ARNOLDI, st, 2);
-    int k = 0;
     for (int j = 0; j < R; ++j) {
-      double2 *vj = dsm ? v.vin() : v.V() + (int64_t)j * n;
-      double2 *zj = v.Z() + (int64_t)j * n;
-      rc = run_apply(ctx, vj, zj, scratch, st);
+      const double2 *vj = dsm ? K.vin() : K.V() + (int64_t)j * n;
+      const int64_t vjs = dsm ? n : K.ldvr();
+      double2 *zj = K.Z() + (int64_t)j * n;
+      const int64_t zs = n * R;
+      rc = run_apply(ctx, vj, vjs, zj, zs, B, scratch, st);
       if (rc) return rc;
       tic(ctx, T_MATVEC, st);
-      KCHK(launch_matvec(ctx, zj, v.w(), st));
+      KCHK(launch_matvec(ctx, zj, zs, K.w(), n, B, st));
       toc(ctx, T_MATVEC, st, 1);
       if (dsm) {
-        KCHK(v.dots_df(j + 1, v.w(), d.h1));
-        KCHK(v.update_df(j + 1, d.h1, v.w(), nullptr));
-        KCHK(v.dots_df(j + 1, v.w(), d.h2));
-        KCHK(v.update_df(j + 1, d.h2, v.w(), d.red));
+        KCHK(K.dots_df(j + 1, K.w(), d.h1, R + 1));
+        KCHK(K.update_df(j + 1, d.h1, R + 1, K.w(), nullptr));
+        KCHK(K.dots_df(j + 1, K.w(), d.h2, R + 1));
+        KCHK(K.update_df(j + 1, d.h2, R + 1, K.w(), d.red));
       } else {
-        KCHK(v.dots(v.V(), j + 1, v.w(), d.h1));
-        KCHK(v.update(v.V(), j + 1, d.h1, -1.0, v.w(), v.w(), nullptr));
-        KCHK(v.dots(v.V(), j + 1, v.w(), d.h2));
-        KCHK(v.update(v.V(), j + 1, d.h2, -1.0, v.w(), v.w(), d.red));
+        KCHK(K.dots(K.V(), K.ldvr(), j + 1, K.w(), d.h1, R + 1));
+        KCHK(K.update(K.V(), K.ldvr(), j + 1, nullptr, d.h1, R + 1, -1.0, K.w(), K.w(), nullptr));
+        KCHK(K.dots(K.V(), K.ldvr(), j + 1, K.w(), d.h2, R + 1));
+        KCHK(K.update(K.V(), K.ldvr(), j + 1, nullptr, d.h2, R + 1, -1.0, K.w(), K.w(), d.red));
       }
       tic(ctx, T_ARNOLDI, st);
-      k_arnoldi_step<<<1, 1, 0, st>>>(d, j);
-      if (dsm) k_scale_df<<<gs, 256, 0, st>>>(v.w(), d.red, 0.0, v.Vdf() + (int64_t)(j + 1) * n, v.vin(), n);
-      else k_scale<<<gs, 256, 0, st>>>(v.w(), d.red, 0.0, v.V() + (int64_t)(j + 1) * n, n);
+      k_arnoldi_step<<<nb, tb, 0, st>>>(d, j);
+      if (dsm) k_scale_df<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.Vdf() + (int64_t)(j + 1) * n, K.ldvr(), K.vin(), n);
+      else k_scale<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.V() + (int64_t)(j + 1) * n, K.ldvr(), n);
       toc(ctx, T_ARNOLDI, st, 2);
       KCHK(cudaGetLastError());
-      KCHK(cudaMemcpyAsync(host_stat, d.stat, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      KCHK(cudaMemcpyAsync(h_stat, d.stat, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, st));
       KCHK(cudaStreamSynchronize(st));
-      ++iters;
-      k = j + 1;
-      if (host_stat[2] != 0.0) { stats->status = HD_ERR_NUMERIC; stats->iters = iters; return HD_ERR_NUMERIC; }
-      stats->relres_est = bnorm > 0 ? host_stat[0] / bnorm : 0.0;
-      if (stats->relres_est <= o->rtol || host_stat[1] == 0.0 || iters >= o->max_iters) break;
+      bool alive = false, changed = false;
+      for (int r = 0; r < B; ++r) {
+        if (!h_live[r]) continue;
+        ++iters[r];
+        h_kcnt[r] = j + 1;
+        const double *sr = h_stat + 4 * r;
+        bool stop = false;
+        if (sr[2] != 0.0) { status[r] = HD_ERR_NUMERIC; done[r] = 1; stop = true; }
+        rel_est[r] = bnorm[r] > 0 ? sr[0] / bnorm[r] : 0.0;
+        if (rel_est[r] <= o->rtol || sr[1] == 0.0 || iters[r] >= o->max_iters) stop = true;
+        if (stop) { h_live[r] = 0; changed = true; }
+        alive = alive || h_live[r];
+      }
+      if (!alive) break;
+      if (changed && (rc = push_masks())) return rc;
     }
+    if ((rc = push_masks())) return rc;   // kcnt for the solution update
     tic(ctx, T_ARNOLDI, st);
-    k_trisolve<<<1, 1, 0, st>>>(d, k);
+    k_trisolve<<<nb, tb, 0, st>>>(d);
     toc(ctx, T_ARNOLDI, st, 1);
-    KCHK(v.update(v.Z(), k, d.y, 1.0, x, x, nullptr));
+    KCHK(K.update(K.Z(), (int64_t)n * R, R, d.kcnt, d.y, R, 1.0, x, x, nullptr));
     ++cycles;
     collect_timers(ctx);
   }
-  stats->iters = iters;
-  stats->restarts = cycles;
-  stats->t_solve_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  if (!stats->converged) stats->status = HD_ERR_NOT_CONVERGED;
-  return stats->status;
+  const double ts = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  int worst = HD_OK;
+  for (int r = 0; r < B; ++r) {
+    hd_gmres_stats &sr = stats[r];
+    sr.iters = iters[r];
+    sr.restarts = cycles;
+    sr.converged = conv[r];
+    sr.relres_est = rel_est[r];
+    sr.relres_true = rel_true[r];
+    sr.t_solve_s = ts;
+    sr.status = status[r] != HD_OK ? status[r] : (conv[r] ? HD_OK : HD_ERR_NOT_CONVERGED);
+    if (sr.status == HD_ERR_NUMERIC) worst = HD_ERR_NUMERIC;
+    else if (sr.status && !worst) worst = sr.status;
+  }
+  return worst;
 }
 
 }  // namespace hd

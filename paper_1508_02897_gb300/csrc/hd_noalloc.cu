@@ -1,5 +1,6 @@
 // Preconditioner application that allocates nothing: the staging vectors of
 // the local substitutions live in a fixed device array of this file.
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -52,7 +53,7 @@ extern "C" int hd_apply_precond_noalloc(hd_ctx *c, const void *r, void *z, int32
     return HD_ERR_INVALID;
   }
   const size_t cs = c->prec == HD_C64 ? sizeof(float2) : sizeof(double2);
-  const size_t need = cs * (size_t)c->staging_elems;
+  const size_t need = cs * (size_t)c->staging_elems;   // one right-hand side
   if (need > kStaticScratchBytes) {
     set_error("hd_apply_precond_noalloc: the staging vectors need " + std::to_string(need) +
               " bytes, more than the library's fixed 64 MiB array; use hd_apply_precond with a caller workspace");
@@ -64,8 +65,11 @@ extern "C" int hd_apply_precond_noalloc(hd_ctx *c, const void *r, void *z, int32
   if (rc) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const int64_t n = (int64_t)c->NX * c->NY;
-  for (int k = 0; k < nrhs; ++k) {
-    rc = run_apply(c, reinterpret_cast<const double2 *>(r) + k * n, reinterpret_cast<double2 *>(z) + k * n, scratch, st);
+  const int group = (int)std::min<size_t>((size_t)nrhs, kStaticScratchBytes / need);
+  for (int k = 0; k < nrhs; k += group) {
+    const int g = std::min(group, nrhs - k);
+    rc = run_apply(c, reinterpret_cast<const double2 *>(r) + k * n, n, reinterpret_cast<double2 *>(z) + k * n, n, g,
+                   scratch, st);
     if (rc) return rc;
   }
   return HD_OK;

@@ -78,13 +78,17 @@ struct OpArgs {
   double h2;
 };
 
-// y = A x on one grid; `mode` 0: y = A x, 1: y = b - A x.
+// y = A x on one grid per blockIdx.z; `mode` 0: y = A x, 1: y = b - A x.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_stencil(OpArgs a, const double2 *__restrict__ x, const double2 *__restrict__ b,
-                                                 double2 *__restrict__ y) {
+__global__ void __launch_bounds__(256) k_stencil(OpArgs a, const double2 *__restrict__ x_all, int64_t xs_,
+                                                 const double2 *__restrict__ b_all, int64_t bs_,
+                                                 double2 *__restrict__ y_all, int64_t ys_) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y;
   if (i >= a.NX) return;
+  const double2 *x = x_all + (int64_t)blockIdx.z * xs_;
+  const double2 *b = MODE == 1 ? b_all + (int64_t)blockIdx.z * bs_ : nullptr;
+  double2 *y = y_all + (int64_t)blockIdx.z * ys_;
   int64_t idx = (int64_t)j * a.NX + i;
   double2 xc = x[idx];
   double2 xw = i > 0 ? x[idx - 1] : make_double2(0.0, 0.0);
@@ -113,15 +117,17 @@ static OpArgs op_args(hd_ctx *ctx) {
   return a;
 }
 
-cudaError_t launch_matvec(hd_ctx *ctx, const double2 *x, double2 *y, cudaStream_t st) {
-  dim3 grid((ctx->NX + 255) / 256, ctx->NY);
-  k_stencil<0><<<grid, 256, 0, st>>>(op_args(ctx), x, nullptr, y);
+cudaError_t launch_matvec(hd_ctx *ctx, const double2 *x, int64_t xs, double2 *y, int64_t ys, int nrhs,
+                          cudaStream_t st) {
+  dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
+  k_stencil<0><<<grid, 256, 0, st>>>(op_args(ctx), x, xs, nullptr, 0, y, ys);
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(hd_ctx *ctx, const double2 *b, const double2 *x, double2 *r, cudaStream_t st) {
-  dim3 grid((ctx->NX + 255) / 256, ctx->NY);
-  k_stencil<1><<<grid, 256, 0, st>>>(op_args(ctx), x, b, r);
+cudaError_t launch_residual(hd_ctx *ctx, const double2 *b, const double2 *x, double2 *r, int nrhs, cudaStream_t st) {
+  const int64_t n = (int64_t)ctx->NX * ctx->NY;
+  dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
+  k_stencil<1><<<grid, 256, 0, st>>>(op_args(ctx), x, n, b, n, r, n);
   return cudaGetLastError();
 }
 

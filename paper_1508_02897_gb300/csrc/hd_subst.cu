@@ -72,28 +72,32 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
 
 template <typename T> __host__ __device__ constexpr int chunk_cols() { return sizeof(T) == 8 ? 4 : 2; }
 
-// Shared memory layout: ring [NS][CH*ldm] | vs [ldmax] | full[NS] | empty[NS] | abort
+// Shared memory layout: ring [NS][CH*ldmax] | vs [NR][ldmax] | full[NS] | empty[NS] | abort
 template <typename T>
-__host__ __device__ inline size_t subst_smem(int ns, int ldmax) {
+__host__ __device__ inline size_t subst_smem(int ns, int ldmax, int nr) {
   size_t stage = (size_t)chunk_cols<T>() * ldmax * sizeof(T);
-  size_t o = (size_t)ns * stage + (size_t)ldmax * sizeof(T);
+  size_t o = (size_t)ns * stage + (size_t)nr * ldmax * sizeof(T);
   o = (o + 15) & ~(size_t)15;
   return o + 2 * (size_t)ns * sizeof(uint64_t) + 16;
 }
 
-template <typename R, int CT, int NA>
+// One CTA per (box, group of NR right-hand sides): every factor block is read
+// once per group and applied to NR vectors.
+template <typename R, int CT, int NA, int NR>
 __global__ void __launch_bounds__(CT + 32)
 k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const C<R> *__restrict__ factor,
-        const double2 *__restrict__ rg, int NX, C<R> *__restrict__ staging, int NS, int ldmax, int32_t *status) {
+        const double2 *__restrict__ rg, int NX, int64_t vec_stride, C<R> *__restrict__ staging, int64_t stg_stride,
+        int nrhs, int NS, int ldmax, int32_t *status) {
   using T = C<R>;
   constexpr int CH = chunk_cols<T>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const SubDev s = subs[blockIdx.x];
   const int m = s.ex, rows = s.ey, ldm = s.ldm;
+  const int r0 = blockIdx.y * NR;
   const size_t stage_elems = (size_t)CH * ldmax;
   T *ring = reinterpret_cast<T *>(smem_raw);
-  T *vs = ring + (size_t)NS * stage_elems;
-  size_t off = ((size_t)NS * stage_elems + ldmax) * sizeof(T);
+  T *vs = ring + (size_t)NS * stage_elems;     // [NR][ldmax]
+  size_t off = ((size_t)NS * stage_elems + (size_t)NR * ldmax) * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + off);
   uint64_t *empty = full + NS;
@@ -146,8 +150,7 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
   const double2 *a1c = pool + s.aoff;
   const double2 *a2c = a1c + 2 * m + 1;
   const double2 *ia2f = a2c + rows;
-  T *stg = staging + s.soff;
-  T a1[NA], w[NA];
+  T a1[NA], w[NA][NR];
   bool ownx[NA];
 #pragma unroll
   for (int e = 0; e < NA; ++e) {
@@ -156,7 +159,8 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
     ownx[e] = a < m && gx >= s.ox0 && gx < s.ox1;
     const double2 t = a < m ? a1c[a] : make_double2(0, 0);
     a1[e] = mk<T>((R)t.x, (R)t.y);
-    w[e] = mk<T>(0, 0);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) w[e][q] = mk<T>(0, 0);
   }
   int64_t it = 0;
   bool ok = true;
@@ -173,12 +177,16 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
       for (int e = 0; e < NA; ++e) {
         const int a = tid + CT * e;
         if (a < m) {
-          T rho = mk<T>(0, 0);
-          if (owny && ownx[e]) {
-            const double2 rv = rg[(int64_t)gy * NX + s.ex0 + a];
-            rho = mk<T>((R)rv.x, (R)rv.y);
+          const T la = cmul(a1[e], is);
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            T rho = mk<T>(0, 0);
+            if (owny && ownx[e] && r0 + q < nrhs) {
+              const double2 rv = rg[(int64_t)(r0 + q) * vec_stride + (int64_t)gy * NX + s.ex0 + a];
+              rho = mk<T>((R)rv.x, (R)rv.y);
+            }
+            vs[q * ldmax + a] = j > 0 ? cfms(la, w[e][q], rho) : rho;   // rho_j - L_j w_{j-1}
           }
-          vs[a] = j > 0 ? cfms(cmul(a1[e], is), w[e], rho) : rho;   // rho_j - L_j w_{j-1}
         }
       }
     } else {
@@ -187,13 +195,19 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
 #pragma unroll
       for (int e = 0; e < NA; ++e) {
         const int a = tid + CT * e;
-        if (a < m) vs[a] = cmul(cmul(a1[e], in), w[e]);             // U_j x_{j+1}
+        if (a < m) {
+          const T ua = cmul(a1[e], in);
+#pragma unroll
+          for (int q = 0; q < NR; ++q) vs[q * ldmax + a] = cmul(ua, w[e][q]);   // U_j x_{j+1}
+        }
       }
     }
     consumer_sync(CT);
-    T acc[NA];
+    T acc[NA][NR];
 #pragma unroll
-    for (int e = 0; e < NA; ++e) acc[e] = mk<T>(0, 0);
+    for (int e = 0; e < NA; ++e)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) acc[e][q] = mk<T>(0, 0);
     for (int c = 0; c < nck; ++c, ++it) {
       const int slot = (int)(it % NS);
       if (ok && !mbar_wait(&full[slot], (uint32_t)((it / NS) & 1), abort_flag)) {
@@ -207,11 +221,17 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
 #pragma unroll
       for (int b = 0; b < CH; ++b) {
         if (b < cols) {
-          const T vb = vs[b0 + b];
+          T sv[NA];
 #pragma unroll
           for (int e = 0; e < NA; ++e) {
             const int a = tid + CT * e;
-            if (a < m) acc[e] = cfma(blk[b * ldm + a], vb, acc[e]);
+            sv[e] = a < m ? blk[b * ldm + a] : mk<T>(0, 0);
+          }
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            const T vb = vs[q * ldmax + b0 + b];
+#pragma unroll
+            for (int e = 0; e < NA; ++e) acc[e][q] = cfma(sv[e], vb, acc[e][q]);
           }
         }
       }
@@ -219,16 +239,21 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
       if (lane == 0) mbar_arrive(&empty[slot]);
     }
 #pragma unroll
-    for (int e = 0; e < NA; ++e) {
-      const int a = tid + CT * e;
-      if (a < m) {
-        if (fwd) {
-          w[e] = acc[e];
-          stg[(int64_t)j * m + a] = acc[e];
-        } else {
-          const T x = csub(stg[(int64_t)j * m + a], acc[e]);
-          w[e] = x;
-          stg[(int64_t)j * m + a] = x;
+    for (int q = 0; q < NR; ++q) {
+      if (r0 + q >= nrhs) continue;
+      T *stg = staging + (int64_t)(r0 + q) * stg_stride + s.soff;
+#pragma unroll
+      for (int e = 0; e < NA; ++e) {
+        const int a = tid + CT * e;
+        if (a < m) {
+          if (fwd) {
+            w[e][q] = acc[e][q];
+            stg[(int64_t)j * m + a] = acc[e][q];
+          } else {
+            const T x = csub(stg[(int64_t)j * m + a], acc[e][q]);
+            w[e][q] = x;
+            stg[(int64_t)j * m + a] = x;
+          }
         }
       }
     }
@@ -239,9 +264,12 @@ template <typename R>
 __global__ void __launch_bounds__(256)
 k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const AxisDev *__restrict__ axy,
          const int32_t *__restrict__ nearx, const int32_t *__restrict__ neary, int nbx, int nby,
-         const C<R> *__restrict__ staging, double2 *__restrict__ z, int NX) {
+         const C<R> *__restrict__ staging_all, int64_t stg_stride, double2 *__restrict__ z_all, int64_t vec_stride,
+         int NX) {
   int gx = blockIdx.x * blockDim.x + threadIdx.x;
   int gy = blockIdx.y;
+  const C<R> *staging = staging_all + (int64_t)blockIdx.z * stg_stride;
+  double2 *z = z_all + (int64_t)blockIdx.z * vec_stride;
   if (gx >= NX) return;
   const int ix = nearx[gx], iy = neary[gy];
   double2 acc = make_double2(0.0, 0.0);
@@ -263,59 +291,83 @@ k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const
 
 // Ring depth: as deep as shared memory allows for the CTAs that share an SM.
 template <typename T>
-static int ring_stages(const hd_ctx *ctx, int ldmax) {
+static int ring_stages(const hd_ctx *ctx, int ldmax, int nr, int groups) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int per_sm = (ctx->nsub + sms - 1) / sms;
+  const int64_t ctas = (int64_t)ctx->nsub * groups;
+  const int per_sm = (int)std::min<int64_t>(7, (ctas + sms - 1) / sms);
   const size_t budget = (size_t)200 * 1024 / (size_t)std::max(1, per_sm);
   const size_t stage = (size_t)chunk_cols<T>() * ldmax * sizeof(T);
-  int ns = (int)(budget / stage);
+  const size_t fixed = (size_t)nr * ldmax * sizeof(T) + 64;
+  int ns = budget > fixed ? (int)((budget - fixed) / stage) : 2;
   return std::min(32, std::max(2, ns));
 }
+
+// Right-hand sides per CTA: one factor read serves NR vectors.
+static int rhs_per_cta(int nrhs) { return nrhs >= 8 ? 8 : (nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1)); }
 
 size_t subst_ring_bytes(const hd_ctx *ctx, int *stages) {
   const int ldmax = (ctx->max_m + 1) & ~1;
   if (ctx->prec == HD_C64) {
-    int ns = ring_stages<float2>(ctx, ldmax);
+    int ns = ring_stages<float2>(ctx, ldmax, 1, 1);
     if (stages) *stages = ns;
-    return subst_smem<float2>(ns, ldmax);
+    return subst_smem<float2>(ns, ldmax, 1);
   }
-  int ns = ring_stages<double2>(ctx, ldmax);
+  int ns = ring_stages<double2>(ctx, ldmax, 1, 1);
   if (stages) *stages = ns;
-  return subst_smem<double2>(ns, ldmax);
+  return subst_smem<double2>(ns, ldmax, 1);
 }
 
-template <typename R, int CT>
-static cudaError_t launch_subst(hd_ctx *ctx, const double2 *r, void *staging, cudaStream_t st) {
+template <typename R, int CT, int NR>
+static cudaError_t launch_subst(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec_stride, void *staging,
+                                int64_t stg_stride, cudaStream_t st) {
   using T = C<R>;
   const int ldmax = (ctx->max_m + 1) & ~1;
-  const int ns = ring_stages<T>(ctx, ldmax);
-  const size_t smem = subst_smem<T>(ns, ldmax);
-  cudaError_t e = cudaFuncSetAttribute(k_subst<R, CT, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int groups = (nrhs + NR - 1) / NR;
+  const int ns = ring_stages<T>(ctx, ldmax, NR, groups);
+  const size_t smem = subst_smem<T>(ns, ldmax, NR);
+  cudaError_t e = cudaFuncSetAttribute(k_subst<R, CT, 2, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_subst<R, CT, 2><<<ctx->nsub, CT + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,
-                                                      reinterpret_cast<const T *>(ctx->factor), r, ctx->NX,
-                                                      reinterpret_cast<T *>(staging), ns, ldmax, ctx->d_status);
+  dim3 grid(ctx->nsub, groups);
+  k_subst<R, CT, 2, NR><<<grid, CT + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,
+                                                     reinterpret_cast<const T *>(ctx->factor), r, ctx->NX, vec_stride,
+                                                     reinterpret_cast<T *>(staging), stg_stride, nrhs, ns, ldmax,
+                                                     ctx->d_status);
   return cudaGetLastError();
 }
 
+template <typename R, int CT>
+static cudaError_t launch_subst_nr(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vs, void *stg, int64_t ss,
+                                   cudaStream_t st) {
+  switch (rhs_per_cta(nrhs)) {
+    case 8: return launch_subst<R, CT, 8>(ctx, r, nrhs, vs, stg, ss, st);
+    case 4: return launch_subst<R, CT, 4>(ctx, r, nrhs, vs, stg, ss, st);
+    case 2: return launch_subst<R, CT, 2>(ctx, r, nrhs, vs, stg, ss, st);
+    default: return launch_subst<R, CT, 1>(ctx, r, nrhs, vs, stg, ss, st);
+  }
+}
+
 template <typename R>
-static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st) {
+static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs,
+                                  void *staging, cudaStream_t st) {
   tic(ctx, T_SUBST, st);
-  cudaError_t e = ctx->max_m <= 192 ? launch_subst<R, 96>(ctx, r, staging, st) : launch_subst<R, 128>(ctx, r, staging, st);
+  cudaError_t e = ctx->max_m <= 192 ? launch_subst_nr<R, 96>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
+                                    : launch_subst_nr<R, 128>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st);
   toc(ctx, T_SUBST, st, 1);
   if (e != cudaSuccess) return e;
-  dim3 grid((ctx->NX + 255) / 256, ctx->NY);
+  dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
   tic(ctx, T_GATHER, st);
   k_gather<R><<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
-                                    ctx->nby, reinterpret_cast<const C<R> *>(staging), z, ctx->NX);
+                                    ctx->nby, reinterpret_cast<const C<R> *>(staging), ctx->staging_elems, z, zs,
+                                    ctx->NX);
   toc(ctx, T_GATHER, st, 1);
   return cudaGetLastError();
 }
 
-int run_apply(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st) {
-  cudaError_t e = ctx->prec == HD_C64 ? launch_apply_r<float>(ctx, r, z, staging, st)
-                                      : launch_apply_r<double>(ctx, r, z, staging, st);
+int run_apply(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs, void *staging,
+              cudaStream_t st) {
+  cudaError_t e = ctx->prec == HD_C64 ? launch_apply_r<float>(ctx, r, rs, z, zs, nrhs, staging, st)
+                                      : launch_apply_r<double>(ctx, r, rs, z, zs, nrhs, staging, st);
   if (e != cudaSuccess) return cuda_fail(e, "preconditioner launch");
   return HD_OK;
 }

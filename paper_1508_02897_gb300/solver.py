@@ -81,12 +81,16 @@ class HelmholtzDDM:
                            self._st())
         return z
 
-    def krylov_workspace(self, restart: int):
-        if restart not in self._krylov:
-            _, kb, _ = B.hd_query_workspace(self.ctx, 1, restart)
+    def krylov_workspace(self, restart: int, nrhs: int = 1):
+        key = (restart, nrhs)
+        if key not in self._krylov:
+            _, kb, sb = B.hd_query_workspace(self.ctx, nrhs, restart)
             self._krylov.clear()
-            self._krylov[restart] = torch.empty(kb, dtype=torch.uint8, device=self.device)
-        return self._krylov[restart]
+            self._krylov[key] = torch.empty(kb, dtype=torch.uint8, device=self.device)
+            if sb > self.scratch_bytes:
+                self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+                self.scratch_bytes = sb
+        return self._krylov[key]
 
     def solve(self, b, restart: int = 50, rtol: float = 1e-8, max_iters: int = 1000, x0=None, out=None,
               arnoldi: str = "auto"):
@@ -99,7 +103,7 @@ class HelmholtzDDM:
             x = self._vec(x0)[0].clone()
         else:
             x = torch.empty_like(b)
-        kws = self.krylov_workspace(restart)
+        kws = self.krylov_workspace(restart, nrhs)
         rc, stats = B.hd_gmres_solve(self.ctx, b.data_ptr(), x.data_ptr(), nrhs, restart, max_iters, rtol,
                                      kws.data_ptr(), kws.numel(), self.scratch.data_ptr(), self.scratch_bytes,
                                      self._st(), use_x0=int(x0 is not None), arnoldi=self._arnoldi(arnoldi))
@@ -146,3 +150,52 @@ def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: i
     s.close()
     h2d = c_d.numel() * c_d.element_size() + f_d.numel() * f_d.element_size()
     return x_h, stats, h2d, x_h.numel() * x_h.element_size()
+
+
+class Server:
+    """Continuous-batching solve server (hd_server_*): requests of any grid,
+    medium and number of sources run concurrently within an HBM budget."""
+
+    def __init__(self, hbm_budget_bytes: int = 160 << 30, max_slots: int = 4, device: int = 0):
+        self.srv = B.hd_server_create(hbm_budget_bytes, max_slots, device)
+        self._keep = {}
+
+    def submit(self, c, f, N, npml, omega, nbx, nby, overlap, restart, rtol, max_iters=5000, precision="c64",
+               cut_x=None, cut_y=None, arnoldi="auto"):
+        """c: float64 [n][n], f: complex128 [nrhs][n][n] host arrays.  Returns a ticket."""
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        f = np.ascontiguousarray(f, dtype=np.complex128)
+        if f.ndim == 2:
+            f = f[None]
+        x = np.empty_like(f)
+        prec = {"c64": B.HD_C64, "c128": B.HD_C128}[precision]
+        mode = arnoldi if arnoldi != "auto" else ("ds" if prec == B.HD_C64 else "fp64")
+        t = B.hd_submit(self.srv, N, N, npml, 1.0 / N, omega, c.ctypes.data, f.ctypes.data, f.shape[0], prec,
+                        restart, max_iters, rtol, x.ctypes.data, nbx, nby, overlap, cut_x, cut_y,
+                        arnoldi={"fp64": B.HD_ARNOLDI_FP64, "ds": B.HD_ARNOLDI_DS}[mode])
+        self._keep[t] = (c, f, x)
+        return t
+
+    def poll(self, ticket, timeout_s=None):
+        """(x, stats, info) once done, None while pending (timeout_s None waits forever)."""
+        c, f, x = self._keep[ticket]
+        us = -1 if timeout_s is None else int(timeout_s * 1e6)
+        rc, stats, info = B.hd_poll(self.srv, ticket, f.shape[0], us)
+        if rc == B.HD_PENDING:
+            return None
+        del self._keep[ticket]
+        return x, stats, info
+
+    def info(self):
+        return B.hd_server_info(self.srv)
+
+    def close(self):
+        if getattr(self, "srv", None):
+            B.hd_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

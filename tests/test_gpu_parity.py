@@ -150,3 +150,48 @@ def test_one_box_is_exact():
     assert st[0]["iters"] == 1 and st[0]["converged"] == 1
     xn = x.cpu().numpy().ravel()
     assert np.linalg.norm(b.ravel() - A @ xn) / np.linalg.norm(b) < 1e-11
+
+
+# ---------------------------------------------------------------- several right-hand sides
+def _sources(case, k, seed):
+    rng = np.random.default_rng(seed)
+    N, npml = case["N"], case["npml"]
+    return np.stack([W.gaussian_source(N, npml, *rng.uniform(0.15, 0.85, 2), 2.0 / N) for _ in range(k)])
+
+
+@pytest.mark.parametrize("precision,nrhs", [("c128", 3), ("c64", 9)])
+def test_precond_batched_equals_single(precision, nrhs):
+    """Each right-hand side of a batched application (groups of up to 8 per CTA)
+    gives bitwise the same vector as its own application."""
+    _, _, g, _, P = oracle("ragged")
+    s = gpu("ragged", precision)
+    r = W.random_complex((nrhs, g.n, g.n), seed=12)
+    from paper_1508_02897_gb300 import _binding as B
+    _, _, need = B.hd_query_workspace(s.ctx, nrhs, 1)
+    s.scratch = torch.empty(need, dtype=torch.uint8, device="cuda")
+    s.scratch_bytes = need
+    z = s.apply_precond(torch.from_numpy(r)).cpu().numpy()
+    for k in range(nrhs):
+        zk = s.apply_precond(torch.from_numpy(r[k])).cpu().numpy()
+        assert np.array_equal(z[k], zk)
+    tol = 1e-10 if precision == "c128" else 2e-4
+    assert rel(z[nrhs - 1], P.apply(r[nrhs - 1])) < tol
+
+
+@pytest.mark.parametrize("precision", ["c128", "c64"])
+def test_gmres_batched_alone_vs_mix(precision):
+    """Lockstep solve of several sources sharing one factorisation: every
+    solution is bitwise the one its source gets alone, and matches the oracle."""
+    case, c, g, A, P = oracle("layers4")
+    s = gpu("layers4", precision)
+    f = _sources(case, 3, seed=5)
+    b = np.stack([rhs_from_source(g, fk) for fk in f])
+    xb, stb = s.solve(torch.from_numpy(b), restart=20, rtol=1e-8, max_iters=300)
+    xb = xb.cpu().numpy()
+    for k in range(3):
+        xk, stk = s.solve(torch.from_numpy(b[k]), restart=20, rtol=1e-8, max_iters=300)
+        assert stb[k]["iters"] == stk[0]["iters"] and stb[k]["converged"] == 1
+        assert np.array_equal(xb[k], xk.cpu().numpy())
+        assert np.linalg.norm(b[k].ravel() - A @ xb[k].ravel()) / np.linalg.norm(b[k]) <= 1e-8
+    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b[1], restart=20, rtol=1e-10, max_iters=400)
+    assert rel(xb[1].ravel(), ref.x) < (1e-7 if precision == "c128" else 1e-5)
