@@ -52,7 +52,7 @@ def parse():
     p.add_argument("--max-requests", type=int, default=0, help="serving: cap on the number of requests (0: none)")
     p.add_argument("--slots", type=int, default=4)
     p.add_argument("--budget-gb", type=float, default=160.0)
-    p.add_argument("--precision", default="c64", choices=("c64", "c128"))
+    p.add_argument("--precision", default="c64", choices=("c64", "c64h", "c128"))
     p.add_argument("--restart", type=int, default=None)
     p.add_argument("--rtol", type=float, default=None)
     p.add_argument("--max-iters", type=int, default=3000)
@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-boxes", type=int, default=2)
     p.add_argument("--arnoldi", default="auto", choices=("auto", "fp64", "ds"))
+    p.add_argument("--no-autotune", dest="autotune", action="store_false")
+    p.add_argument("--symmetric", action="store_true", help="store only the upper tiles of each S_j^{-1}")
     p.add_argument("--nrhs", type=int, default=None, help="sources per solve (batching config: 64)")
     p.add_argument("--group", type=int, default=16, help="sources solved together in lockstep")
     p.add_argument("--single-sample", type=int, default=2, help="batching: sources also solved one at a time")
@@ -185,7 +187,7 @@ def _rhs_per_cta(k):
     return 8 if k >= 8 else (4 if k >= 4 else (2 if k >= 2 else 1))
 
 
-def subst_bytes(wl, cs: int, nrhs: int = 1) -> int:
+def subst_bytes(wl, cs: int, nrhs: int = 1, fs: int = None) -> int:
     """Algorithmic HBM bytes of one k_subst launch (one preconditioner application
     to nrhs vectors): every stored S_j^{-1} read once forward and once backward (the
     last row once) per group of right-hand sides sharing a CTA, the owned residual
@@ -197,7 +199,7 @@ def subst_bytes(wl, cs: int, nrhs: int = 1) -> int:
         for ix in range(wl.nbx):
             m = _extent(wl.cut_x, ix, wl)
             rows = _extent(wl.cut_y, iy, wl)
-            tot += (2 * rows - 1) * m * m * cs * groups + 3 * rows * m * cs * nrhs
+            tot += (2 * rows - 1) * m * m * (fs or cs) * groups + 3 * rows * m * cs * nrhs
     return tot
 
 
@@ -231,9 +233,11 @@ def run_ours(args, world, rank, local):
         f = f_d if f is None else f
         grp = group if grp is None else grp
         s = HelmholtzDDM(wl.N, wl.npml, wl.omega, c_d, wl.nbx, wl.nby, wl.overlap, precision=precision,
-                         cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev))
+                         cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev), symmetric=args.symmetric)
         s.set_profiling(profile)
         s.factor()
+        if args.autotune:
+            s.autotune()   # launch shape of the substitution: timed once per process, then cached
         sts = []
         for g0 in range(0, f.shape[0], grp):
             b = s.rhs(f[g0:g0 + grp])
@@ -275,8 +279,9 @@ def run_ours(args, world, rank, local):
     cls_ms = {c: sum(t[c][0] for t in timers) for c in classes}
     cls_n = {c: sum(t[c][1] for t in timers) for c in classes}
     launches = int(sum(cls_n.values()))
-    cs = 8 if args.precision == "c64" else 16
-    sb = subst_bytes(wl, cs, group)
+    cs = 16 if args.precision == "c128" else 8                       # staging (compute) entry
+    fs = {"c128": 16, "c64": 8, "c64h": 4}[args.precision]          # stored factor entry
+    sb = subst_bytes(wl, cs, group, fs)
     sub_avg_ms = cls_ms["subst"] / max(cls_n["subst"], 1)
     achieved = sb / (sub_avg_ms / 1e3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -297,19 +302,19 @@ def run_ours(args, world, rank, local):
             arn_flops += 32 * (j + 1) * n_unk
             arn_bytes += 4 * (j + 1) * n_unk * 16 + 8 * n_unk * 16
     arn_s = cls_ms["arnoldi"] / 1e3
-    ds_mode = args.arnoldi == "ds" or (args.arnoldi == "auto" and args.precision == "c64")
+    ds_mode = args.arnoldi == "ds" or (args.arnoldi == "auto" and args.precision != "c128")
 
     out = {
         "metric": METRIC, "value": solves / total_max_s, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_max_s * 1e3 / args.steps,
         "sources_per_step": wl.nrhs, "lockstep_group": group,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "c64+f64" if args.precision == "c64" else "f64",
+        "dtype": {"c64": "c64+f64", "c64h": "c32(storage)/c64+f64", "c128": "f64"}[args.precision],
         "data": "synthetic (seeded random medium and Gaussian source; no dataset)",
         "config": {"workload": describe(wl, args.precision), "N": wl.N, "npml": wl.npml, "boxes": [wl.nbx, wl.nby],
                    "overlap": wl.overlap, "restart": wl.restart, "rtol": wl.rtol, "precision": args.precision,
                    "omega": wl.omega, "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)" % (
-                       _factor_gb(wl, cs), 2 * (wl.restart + 1) * n_unk * 16 / 1e9),
+                       _factor_gb(wl, fs), 2 * (wl.restart + 1) * n_unk * 16 / 1e9),
                    "parallelism": f"replicas x{world} (one independent solve per GPU)"},
         "unknown_iters_per_s": unk_iters,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -429,8 +434,9 @@ def _profile_traffic(wl, args):
         d = json.load(open(path))
         if d.get("precision") != args.precision or d.get("kernel_rev") != KERNEL_REV:
             return None
-        cs = 8 if args.precision == "c64" else 16
-        return d["dram_bytes_per_launch"] * subst_bytes(wl, cs) / d["algorithmic_bytes_per_launch"]
+        cs = 16 if args.precision == "c128" else 8
+        fs = {"c128": 16, "c64": 8, "c64h": 4}[args.precision]
+        return d["dram_bytes_per_launch"] * subst_bytes(wl, cs, 1, fs) / d["algorithmic_bytes_per_launch"]
     except Exception:
         return None
 

@@ -49,8 +49,18 @@ typedef enum {
 
 typedef enum {
   HD_C128 = 0,  /* local factors and substitutions in complex FP64              */
-  HD_C64 = 1    /* local factors and substitutions in complex FP32, FP64 outside */
+  HD_C64 = 1,   /* local factors and substitutions in complex FP32, FP64 outside */
+  HD_C64_H = 2  /* as HD_C64, but the stored S_j^{-1} are complex FP16 (half the
+                   bytes streamed by every preconditioner application); the
+                   factorisation recursion itself stays FP32                     */
 } hd_precision;
+
+/* Flag OR-ed into the precision of hd_setup_medium: store only the upper
+ * 16 x 16 tiles of every S_j^{-1} (which is complex symmetric, because the
+ * operator is), so each preconditioner application streams about 55% of the
+ * bytes; the stored inverse is the exactly symmetric matrix built from the
+ * computed inverse's upper triangle. */
+#define HD_SYMMETRIC 0x100
 
 /* Truncated domain Omega of Sec. 2: interior nx x ny cells of width h (the
  * interior is [0, nx h] x [0, ny h]), npml PML cells per side.  The PML uses
@@ -170,6 +180,9 @@ typedef struct {
   double rtol;        /* stop when ||b - A x|| <= rtol ||b||                        */
   int32_t use_x0;     /* 1: start from x_dev, 0: x0 = 0                              */
   int32_t arnoldi;    /* hd_arnoldi_mode                                            */
+  int32_t graphs;     /* 1: capture each Arnoldi step j (preconditioner, matvec, CGS2,
+                         Givens, scaling) once as a CUDA graph per workspace and
+                         replay it in later cycles and solves; 0: plain launches   */
 } hd_gmres_opts;
 
 typedef struct {
@@ -197,6 +210,19 @@ typedef struct {
 int hd_gmres_solve(hd_ctx *ctx, const void *b_dev, void *x_dev, int32_t nrhs, const hd_gmres_opts *opts,
                    void *krylov_dev, size_t krylov_bytes, void *scratch_dev, size_t scratch_bytes,
                    hd_gmres_stats *stats_host, void *stream);
+
+/* Autotuner (no counterpart in the paper): times hd_apply_precond's
+ * substitution kernel for each candidate launch shape (96, 128, 192 or 256
+ * consumer threads per CTA, 2 to 32 ring stages that fit shared memory) on r_dev ->
+ * z_dev (complex128 NY x NX, contents irrelevant, z is overwritten) with CUDA
+ * events on `stream`, and keeps the fastest for this context.  The choice is
+ * remembered for the process per (precision, storage layout, widest box,
+ * number of boxes, device), so later contexts of the same shape reuse it without timing.
+ * Needs a prior hd_factor_subdomains; synchronises `stream`.  Any output
+ * pointer may be NULL; *ms_out is the winner's time per application (-1 when
+ * taken from the cache). */
+int hd_autotune(hd_ctx *ctx, const void *r_dev, void *z_dev, void *scratch_dev, size_t scratch_bytes,
+                int32_t *threads_out, int32_t *stages_out, float *ms_out, void *stream);
 
 /* Per-kernel-class timing with CUDA events recorded on the launching stream
  * (events only while profiling is on; off by default).  Classes: 0

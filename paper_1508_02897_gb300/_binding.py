@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libhd.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "hd.h")
 
 HD_OK, HD_ERR_INVALID, HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_NOT_CONVERGED, HD_ERR_NUMERIC, HD_ERR_TIMEOUT, HD_PENDING = range(8)
-HD_C128, HD_C64 = 0, 1
+HD_C128, HD_C64, HD_C64_H = 0, 1, 2
+HD_SYMMETRIC = 0x100
 HD_ARNOLDI_FP64, HD_ARNOLDI_DS = 0, 1
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID", 2: "HD_ERR_OOM", 3: "HD_ERR_CUDA", 4: "HD_ERR_NOT_CONVERGED",
                 5: "HD_ERR_NUMERIC", 6: "HD_ERR_TIMEOUT", 7: "HD_PENDING"}
@@ -36,7 +37,7 @@ class hd_decomp(ct.Structure):
 
 class hd_gmres_opts(ct.Structure):
     _fields_ = [("restart", ct.c_int32), ("max_iters", ct.c_int32), ("rtol", ct.c_double), ("use_x0", ct.c_int32),
-                ("arnoldi", ct.c_int32)]
+                ("arnoldi", ct.c_int32), ("graphs", ct.c_int32)]
 
 
 class hd_gmres_stats(ct.Structure):
@@ -82,6 +83,8 @@ _SIGS = {
     "hd_gmres_solve": [_P, _P, _P, ct.c_int32, ct.POINTER(hd_gmres_opts), _P, ct.c_size_t, _P, ct.c_size_t,
                        ct.POINTER(hd_gmres_stats), _P],
     "hd_apply_precond_noalloc": [_P, _P, _P, ct.c_int32, _P],
+    "hd_autotune": [_P, _P, _P, _P, ct.c_size_t, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
+                    ct.POINTER(ct.c_float), _P],
     "hd_set_profiling": [_P, ct.c_int32],
     "hd_get_timers": [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32, ct.c_int32, _P],
     "hd_check_status": [_P, ct.c_int32, _P],
@@ -175,13 +178,21 @@ def hd_apply_precond_noalloc(ctx, r_ptr, z_ptr, nrhs, stream):
 
 
 def hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, restart, max_iters, rtol, krylov_ptr, krylov_bytes, scratch_ptr,
-                   scratch_bytes, stream, use_x0=0, arnoldi=HD_ARNOLDI_FP64, raise_on_not_converged=False):
-    o = hd_gmres_opts(restart, max_iters, rtol, use_x0, arnoldi)
+                   scratch_bytes, stream, use_x0=0, arnoldi=HD_ARNOLDI_FP64, graphs=0, raise_on_not_converged=False):
+    o = hd_gmres_opts(restart, max_iters, rtol, use_x0, arnoldi, graphs)
     st = (hd_gmres_stats * nrhs)()
     allow = () if raise_on_not_converged else (HD_ERR_NOT_CONVERGED,)
     rc = _check("hd_gmres_solve", lib().hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, ct.byref(o), krylov_ptr, krylov_bytes,
                                                        scratch_ptr, scratch_bytes, st, stream), allow)
     return rc, [s.as_dict() for s in st]
+
+
+def hd_autotune(ctx, r_ptr, z_ptr, scratch_ptr, scratch_bytes, stream):
+    """Times the substitution launch shapes and keeps the fastest; returns (threads, stages, ms)."""
+    t, n, ms = ct.c_int32(), ct.c_int32(), ct.c_float()
+    _check("hd_autotune", lib().hd_autotune(ctx, r_ptr, z_ptr, scratch_ptr, scratch_bytes, ct.byref(t), ct.byref(n),
+                                            ct.byref(ms), stream))
+    return t.value, n.value, ms.value
 
 
 def hd_set_profiling(ctx, on):
@@ -226,7 +237,7 @@ def hd_submit(srv, nx, ny, npml, h, omega, c_ptr, f_ptr, nrhs, precision, restar
     kx, px = _cuts(cut_x)
     ky, py = _cuts(cut_y)
     d = hd_decomp(nbx, nby, overlap, px, py, own_global_pml)
-    o = hd_gmres_opts(restart, max_iters, rtol, 0, arnoldi)
+    o = hd_gmres_opts(restart, max_iters, rtol, 0, arnoldi, 0)
     t = ct.c_uint64()
     _check("hd_submit", lib().hd_submit(srv, ct.byref(g), ct.byref(d), c_ptr, f_ptr, nrhs, precision, ct.byref(o),
                                         x_ptr, ct.byref(t)))

@@ -72,6 +72,12 @@ int collect_timers(hd_ctx *ctx) {
 
 static void free_ctx(hd_ctx *c) {
   if (!c) return;
+  for (auto &g : c->graphs) cudaGraphExecDestroy(g.second.exec);
+  if (c->gstream) {
+    cudaStreamSynchronize(c->gstream);
+    cudaStreamDestroy(c->gstream);
+  }
+  if (c->gevent) cudaEventDestroy(c->gevent);
   if (c->d_k2) cudaFreeAsync(c->d_k2, c->stream);
   if (c->d_gax_c) cudaFreeAsync(c->d_gax_c, c->stream);
   if (c->d_giax_f) cudaFreeAsync(c->d_giax_f, c->stream);
@@ -143,14 +149,17 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
     return invalid("hd_setup_medium: bad grid");
   if (dec->nbx < 1 || dec->nby < 1 || dec->overlap < 0 || dec->nbx > grid->nx || dec->nby > grid->ny)
     return invalid("hd_setup_medium: bad decomposition");
-  if (precision != HD_C128 && precision != HD_C64) return invalid("hd_setup_medium: bad precision");
+  const int base_prec = precision & 0xff;
+  if ((base_prec != HD_C128 && base_prec != HD_C64 && base_prec != HD_C64_H) || (precision & ~(0xff | HD_SYMMETRIC)))
+    return invalid("hd_setup_medium: bad precision");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   hd_ctx *c = new (std::nothrow) hd_ctx();
   if (!c) { set_error("hd_setup_medium: host allocation failed"); return HD_ERR_OOM; }
   c->nx_in = grid->nx; c->ny_in = grid->ny; c->npml = grid->npml;
   c->NX = grid->nx + 2 * grid->npml; c->NY = grid->ny + 2 * grid->npml;
   c->h = grid->h; c->omega = grid->omega; c->s0 = grid->sigma0_over_omega; c->power = grid->pml_power;
-  c->prec = precision;
+  c->prec = base_prec;
+  c->sym = (precision & HD_SYMMETRIC) != 0;
   c->stream = st;
   c->nbx = dec->nbx; c->nby = dec->nby; c->overlap = dec->overlap; c->own_global_pml = dec->own_global_pml ? 1 : 0;
   std::vector<int32_t> nearx, neary;
@@ -169,11 +178,12 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
       s.ex0 = ax.e0; s.ex = ax.e1 - ax.e0; s.ey0 = ay.e0; s.ey = ay.e1 - ay.e0;
       s.ox0 = ax.o0; s.ox1 = ax.o1; s.oy0 = ay.o0; s.oy1 = ay.o1;
       s.ix = ix; s.iy = iy;
-      s.ldm = (s.ex + 1) & ~1;
+      s.ldm = (s.ex + 3) & ~3;
       s.pad_ = 0;
-      s.foff = foff; foff += (int64_t)s.ey * s.ex * s.ldm;
+      const int64_t mt = (s.ex + 15) / 16;
+      s.foff = foff; foff += c->sym ? (int64_t)s.ey * (mt * (mt + 1) / 2) * 256 : (int64_t)s.ey * s.ex * s.ldm;
       s.soff = soff; soff += (int64_t)s.ex * s.ey;
-      s.woff = woff; woff += (int64_t)s.ex * s.ex;
+      s.woff = woff; woff += 2 * (int64_t)s.ex * s.ex;
       s.aoff = aoff; aoff += 2 * s.ex + 2 * s.ey + 2;
       c->max_m = std::max(c->max_m, s.ex);
       c->max_rows = std::max(c->max_rows, s.ey);
@@ -231,8 +241,8 @@ int hd_query_workspace(const hd_ctx *c, int32_t nrhs, int32_t restart, size_t *f
                        size_t *scratch_bytes) {
   if (!c) return invalid("hd_query_workspace: NULL context");
   if (nrhs < 1 || restart < 1) return invalid("hd_query_workspace: nrhs and restart must be >= 1");
-  size_t cs = c->prec == HD_C64 ? sizeof(float2) : sizeof(double2);
-  if (factor_bytes) *factor_bytes = cs * (size_t)c->factor_elems;
+  const size_t cs = compute_bytes(c->prec);
+  if (factor_bytes) *factor_bytes = store_bytes(c->prec) * (size_t)c->factor_elems;
   if (scratch_bytes) *scratch_bytes = cs * (size_t)std::max(c->staging_elems * (int64_t)nrhs, c->work_elems);
   if (krylov_bytes_out) *krylov_bytes_out = krylov_bytes((int64_t)c->NX * c->NY, restart, nrhs);
   return HD_OK;
@@ -285,7 +295,7 @@ int hd_apply_precond(hd_ctx *c, const void *r, void *z, int32_t nrhs, void *scra
                      void *stream) {
   if (!c || !r || !z || !scratch || nrhs < 1) return invalid("hd_apply_precond: bad argument");
   if (!c->factored) return invalid("hd_apply_precond: call hd_factor_subdomains first");
-  const size_t per = (c->prec == HD_C64 ? sizeof(float2) : sizeof(double2)) * (size_t)c->staging_elems;
+  const size_t per = compute_bytes(c->prec) * (size_t)c->staging_elems;
   if (scratch_bytes < per) { set_error("hd_apply_precond: scratch workspace too small"); return HD_ERR_OOM; }
   if (!aligned16(r) || !aligned16(z) || !aligned16(scratch)) return invalid("hd_apply_precond: buffers must be 16-byte aligned");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -326,6 +336,20 @@ int hd_gmres_solve(hd_ctx *c, const void *b, void *x, int32_t nrhs, const hd_gmr
   if (status) { set_error("hd_gmres_solve: a zero pivot or non-finite value was flagged on the device"); return HD_ERR_NUMERIC; }
   if (rc == HD_ERR_NOT_CONVERGED) set_error("hd_gmres_solve: not converged within max_iters");
   if (rc == HD_ERR_NUMERIC) set_error("hd_gmres_solve: non-finite value in the Arnoldi process");
+  return rc;
+}
+
+int hd_autotune(hd_ctx *c, const void *r, void *z, void *scratch, size_t scratch_bytes, int32_t *threads_out,
+                int32_t *stages_out, float *ms_out, void *stream) {
+  if (!c || !r || !z || !scratch) return invalid("hd_autotune: bad argument");
+  if (!c->factored) return invalid("hd_autotune: call hd_factor_subdomains first");
+  const size_t per = compute_bytes(c->prec) * (size_t)c->staging_elems;
+  if (scratch_bytes < per) { set_error("hd_autotune: scratch workspace too small"); return HD_ERR_OOM; }
+  int ct = 0, ns = 0;
+  int rc = autotune_subst(c, reinterpret_cast<const double2 *>(r), reinterpret_cast<double2 *>(z), scratch,
+                          reinterpret_cast<cudaStream_t>(stream), &ct, &ns, ms_out);
+  if (threads_out) *threads_out = ct;
+  if (stages_out) *stages_out = ns;
   return rc;
 }
 

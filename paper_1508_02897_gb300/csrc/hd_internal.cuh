@@ -1,9 +1,12 @@
 // Internal declarations shared by the translation units of libhd.
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/hd.h"
@@ -62,6 +65,16 @@ __host__ __device__ __forceinline__ double2 to_c(double2 z, double2) { return z;
 __host__ __device__ __forceinline__ double2 to_d(float2 z) { return make_double2(z.x, z.y); }
 __host__ __device__ __forceinline__ double2 to_d(double2 z) { return z; }
 
+// Stored factor entries: the compute type itself, or complex FP16 for FP32 math.
+template <typename S, typename T> __device__ __forceinline__ S store_c(T v) { return v; }
+template <> __device__ __forceinline__ __half2 store_c<__half2, float2>(float2 v) { return __float22half2_rn(v); }
+template <typename T, typename S> __device__ __forceinline__ T load_c(S v) { return v; }
+template <> __device__ __forceinline__ float2 load_c<float2, __half2>(__half2 v) { return __half22float2(v); }
+
+// Bytes of one stored factor entry and of one compute (staging / working) entry.
+inline size_t store_bytes(int prec) { return prec == HD_C128 ? 16 : (prec == HD_C64 ? 8 : 4); }
+inline size_t compute_bytes(int prec) { return prec == HD_C128 ? 16 : 8; }
+
 // ---------------------------------------------------------------- tables
 // One overlapping box Omega_ij (global cell indices) and its owned box.
 struct SubDev {
@@ -72,7 +85,7 @@ struct SubDev {
   int64_t woff;                  // offset of the factorisation working matrix (complex entries)
   int32_t aoff;                  // offset into the local PML table pool
   int32_t ix, iy;
-  int32_t ldm;                   // leading dimension of a stored S_j^{-1} (m rounded up to even)
+  int32_t ldm;                   // leading dimension of a stored S_j^{-1} (m rounded up to a multiple of 4)
   int32_t pad_;
 };
 
@@ -81,10 +94,25 @@ struct AxisDev {
   int32_t e0, e1, o0, o1;
 };
 
+// A captured Arnoldi step (CUDA graph) and the kernels it holds per timer class.
+struct GraphKey {
+  const void *kws, *scratch, *factor;
+  int B, R, ds, j, ct, ns;
+  bool operator<(const GraphKey &o) const {
+    return std::tie(kws, scratch, factor, B, R, ds, j, ct, ns) <
+           std::tie(o.kws, o.scratch, o.factor, o.B, o.R, o.ds, o.j, o.ct, o.ns);
+  }
+};
+
 enum TimerClass { T_FACTOR = 0, T_SUBST = 1, T_GATHER = 2, T_MATVEC = 3, T_ARNOLDI = 4, T_OTHER = 5, T_NCLASS = 6 };
 
 // Bits of the device status word.
 enum StatusBits { ST_ZERO_PIVOT = 1, ST_NONFINITE = 2, ST_TIMEOUT = 4 };
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  int64_t kernels[T_NCLASS] = {0};
+};
 
 }  // namespace hd
 
@@ -94,6 +122,7 @@ struct hd_ctx {
   double h, omega, s0;
   int power;
   int prec;
+  bool sym = false;   // S_j^{-1} stored as upper 16 x 16 tiles (HD_SYMMETRIC)
   // decomposition
   int nbx, nby, overlap, own_global_pml;
   int nsub;
@@ -115,6 +144,12 @@ struct hd_ctx {
   // factor binding
   void *factor = nullptr;
   bool factored = false;
+  // substitution launch shape chosen by hd_autotune (0: built-in heuristic)
+  int tune_ct = 0, tune_ns = 0;
+  // captured Arnoldi steps (hd_gmres_opts.graphs), run on the context's own stream
+  std::map<hd::GraphKey, hd::GraphEntry> graphs;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gevent = nullptr;
   // profiling
   bool profiling = false;
   double t_ms[hd::T_NCLASS] = {0};
@@ -150,8 +185,9 @@ int run_factor(hd_ctx *ctx, void *factor, void *work, cudaStream_t st);
 int run_apply(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs, void *staging,
               cudaStream_t st);
 size_t krylov_bytes(int64_t n, int restart, int nrhs);
+int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st, int *ct_out,
+                   int *ns_out, float *ms_out);
 int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const hd_gmres_opts *o, void *kws,
                     void *scratch, hd_gmres_stats *stats, cudaStream_t st);
-size_t subst_ring_bytes(const hd_ctx *ctx, int *stages);
 size_t factor_smem_bytes(int prec, int max_m);
 }  // namespace hd

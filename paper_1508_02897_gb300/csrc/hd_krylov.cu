@@ -228,23 +228,25 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, i
   for (int k = warp; k < nk; k += 8) {
     const float4 *vk = Vr + (int64_t)k * ldv + base;
     float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-    for (int i0 = 0; i0 < cnt; i0 += 256) {
-      float4 vv[8];
+    for (int i0 = 0; i0 < cnt; i0 += 512) {   // 16 loads of 16 bytes in flight per lane
+      float4 vv[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         int i = i0 + u * 32 + lane;
         vv[u] = i < cnt ? vk[i] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const float4 a = vv[u], b = wsm[i0 + u * 32 + lane];
         ds_mac(rh, rl, a.x, a.y, b.x, b.y);     // re += ar br
         ds_mac(rh, rl, a.z, a.w, b.z, b.w);     // re += ai bi
         ds_mac(ih, il, a.x, a.y, b.z, b.w);     // im += ar bi
         ds_mac(ih, il, -a.z, -a.w, b.x, b.y);   // im -= ai br
+        if ((u & 7) == 7) {
+          ds_renorm(rh, rl);
+          ds_renorm(ih, il);
+        }
       }
-      ds_renorm(rh, rl);
-      ds_renorm(ih, il);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -285,6 +287,7 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
     float rh[E], rl[E], ih[E], il[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) { rh[e] = rl[e] = ih[e] = il[e] = 0.f; }
+#pragma unroll 2
     for (int k = 0; k < nk; ++k) {
       const float4 c = csm[k];
       const float4 *vk = Vr + (int64_t)k * ldv;
@@ -542,8 +545,28 @@ struct Krylov {
   }
 };
 
+static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, const hd_gmres_opts *o, void *kws,
+                              void *scratch, hd_gmres_stats *stats, cudaStream_t st);
+
+// With graphs on, the solve runs on a stream of the context (the legacy default
+// stream cannot be captured), ordered after and before the caller's stream by events.
 int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int B, const hd_gmres_opts *o, void *kws,
                     void *scratch, hd_gmres_stats *stats, cudaStream_t st) {
+  if (!o->graphs) return run_gmres_batch_on(ctx, b, x, B, o, kws, scratch, stats, st);
+  if (!ctx->gstream) {
+    KCHK(cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+    KCHK(cudaEventCreateWithFlags(&ctx->gevent, cudaEventDisableTiming));
+  }
+  KCHK(cudaEventRecord(ctx->gevent, st));
+  KCHK(cudaStreamWaitEvent(ctx->gstream, ctx->gevent, 0));
+  const int rc = run_gmres_batch_on(ctx, b, x, B, o, kws, scratch, stats, ctx->gstream);
+  KCHK(cudaEventRecord(ctx->gevent, ctx->gstream));
+  KCHK(cudaStreamWaitEvent(st, ctx->gevent, 0));
+  return rc;
+}
+
+static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, const hd_gmres_opts *o, void *kws,
+                              void *scratch, hd_gmres_stats *stats, cudaStream_t st) {
   auto t0 = std::chrono::steady_clock::now();
   const int64_t n = (int64_t)ctx->NX * ctx->NY;
   const int R = o->restart;
@@ -625,13 +648,15 @@ int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int B, const hd_g
     if (dsm) k_scale_df<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.Vdf(), K.ldvr(), K.vin(), n);
     else k_scale<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.V(), K.ldvr(), n);
     toc(ctx, T_ARNOLDI, st, 2);
-    for (int j = 0; j < R; ++j) {
+    // One Arnoldi step for every live right-hand side: z_j = M v_j, w = A z_j, CGS2,
+    // Hessenberg/Givens update, v_{j+1} = w / ||w||.
+    auto enqueue_step = [&](int j) -> int {
       const double2 *vj = dsm ? K.vin() : K.V() + (int64_t)j * n;
       const int64_t vjs = dsm ? n : K.ldvr();
       double2 *zj = K.Z() + (int64_t)j * n;
       const int64_t zs = n * R;
-      rc = run_apply(ctx, vj, vjs, zj, zs, B, scratch, st);
-      if (rc) return rc;
+      int rc2 = run_apply(ctx, vj, vjs, zj, zs, B, scratch, st);
+      if (rc2) return rc2;
       tic(ctx, T_MATVEC, st);
       KCHK(launch_matvec(ctx, zj, zs, K.w(), n, B, st));
       toc(ctx, T_MATVEC, st, 1);
@@ -652,6 +677,42 @@ int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int B, const hd_g
       else k_scale<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.V() + (int64_t)(j + 1) * n, K.ldvr(), n);
       toc(ctx, T_ARNOLDI, st, 2);
       KCHK(cudaGetLastError());
+      return HD_OK;
+    };
+    for (int j = 0; j < R; ++j) {
+      if (o->graphs) {
+        // each step j is captured once per workspace/launch shape and then replayed
+        const GraphKey key{kws, scratch, ctx->factor, B, R, dsm ? 1 : 0, j, ctx->tune_ct, ctx->tune_ns};
+        auto it = ctx->graphs.find(key);
+        if (it == ctx->graphs.end()) {
+          const bool prof = ctx->profiling;
+          int64_t before[T_NCLASS];
+          for (int q = 0; q < T_NCLASS; ++q) before[q] = ctx->t_launch[q];
+          ctx->profiling = false;   // no event brackets inside a graph
+          KCHK(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
+          const int rc2 = enqueue_step(j);
+          cudaGraph_t graph = nullptr;
+          const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+          ctx->profiling = prof;
+          if (rc2) { if (graph) cudaGraphDestroy(graph); return rc2; }
+          KCHK(ec);
+          GraphEntry ge;
+          const cudaError_t ei = cudaGraphInstantiate(&ge.exec, graph, 0);
+          cudaGraphDestroy(graph);
+          KCHK(ei);
+          for (int q = 0; q < T_NCLASS; ++q) {
+            ge.kernels[q] = ctx->t_launch[q] - before[q];
+            ctx->t_launch[q] = before[q];
+          }
+          it = ctx->graphs.emplace(key, ge).first;
+        }
+        tic(ctx, T_OTHER, st);
+        KCHK(cudaGraphLaunch(it->second.exec, st));
+        toc(ctx, T_OTHER, st, 0);
+        for (int q = 0; q < T_NCLASS; ++q) ctx->t_launch[q] += it->second.kernels[q];
+      } else {
+        if ((rc = enqueue_step(j))) return rc;
+      }
       KCHK(cudaMemcpyAsync(h_stat, d.stat, sizeof(double) * 4 * B, cudaMemcpyDeviceToHost, st));
       KCHK(cudaStreamSynchronize(st));
       bool alive = false, changed = false;

@@ -52,7 +52,7 @@ extern "C" int hd_apply_precond_noalloc(hd_ctx *c, const void *r, void *z, int32
     set_error("hd_apply_precond_noalloc: vectors must be 16-byte aligned");
     return HD_ERR_INVALID;
   }
-  const size_t cs = c->prec == HD_C64 ? sizeof(float2) : sizeof(double2);
+  const size_t cs = compute_bytes(c->prec);
   const size_t need = cs * (size_t)c->staging_elems;   // one right-hand side
   if (need > kStaticScratchBytes) {
     set_error("hd_apply_precond_noalloc: the staging vectors need " + std::to_string(need) +

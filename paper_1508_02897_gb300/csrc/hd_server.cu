@@ -87,18 +87,20 @@ static size_t request_bytes(const Request &q, int batch) {
   if (!axis_extents(q.grid.nx, q.grid.npml, q.nbx, q.overlap, q.cut_x, ex) ||
       !axis_extents(q.grid.ny, q.grid.npml, q.nby, q.overlap, q.cut_y, ey))
     return (size_t)-1;
-  const size_t cs = q.precision == HD_C64 ? 8 : 16;
+  const size_t cs = compute_bytes(q.precision & 0xff);
+  const bool sym = (q.precision & HD_SYMMETRIC) != 0;
   size_t factor = 0, staging = 0, work = 0;
   for (int a : ey)
     for (int b : ex) {
-      factor += (size_t)a * b * ((b + 1) & ~1);
+      const size_t mt = (b + 15) / 16;
+      factor += sym ? (size_t)a * mt * (mt + 1) / 2 * 256 : (size_t)a * b * ((b + 3) & ~3);
       staging += (size_t)a * b;
-      work += (size_t)b * b;
+      work += 2 * (size_t)b * b;
     }
   const size_t n = (size_t)(q.grid.nx + 2 * q.grid.npml) * (q.grid.ny + 2 * q.grid.npml);
   const size_t tables = n * 8 + ((size_t)1 << 20);
   const size_t vecs = n * 8 + 2 * n * 16 * (size_t)batch;     // velocity, right-hand sides, solutions
-  return cs * factor + cs * std::max(staging * batch, work) + krylov_bytes((int64_t)n, q.opts.restart, batch) +
+  return store_bytes(q.precision & 0xff) * factor + cs * std::max(staging * batch, work) + krylov_bytes((int64_t)n, q.opts.restart, batch) +
          tables + vecs;
 }
 
@@ -228,7 +230,8 @@ int hd_server_create(hd_server **out, size_t hbm_budget_bytes, int32_t max_slots
 int hd_submit(hd_server *s, const hd_grid *grid, const hd_decomp *dec, const double *c_host, const void *f_host,
               int32_t nrhs, int32_t precision, const hd_gmres_opts *opts, void *x_host, uint64_t *ticket) {
   if (!s || !grid || !dec || !c_host || !f_host || !opts || !x_host || !ticket || nrhs < 1 || opts->restart < 1 ||
-      (precision != HD_C64 && precision != HD_C128)) {
+      ((precision & 0xff) != HD_C64 && (precision & 0xff) != HD_C128 && (precision & 0xff) != HD_C64_H) ||
+      (precision & ~(0xff | HD_SYMMETRIC))) {
     set_error("hd_submit: bad argument");
     return HD_ERR_INVALID;
   }

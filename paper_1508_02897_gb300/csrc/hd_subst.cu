@@ -70,12 +70,38 @@ __device__ __forceinline__ void consumer_sync(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-template <typename T> __host__ __device__ constexpr int chunk_cols() { return sizeof(T) == 8 ? 4 : 2; }
+// Columns of a stored factor block per ring stage (about 11 KB at m = 176).
+template <typename S> __host__ __device__ constexpr int chunk_cols() {
+  return sizeof(S) == 16 ? 4 : (sizeof(S) == 8 ? 8 : 16);
+}
 
-// Shared memory layout: ring [NS][CH*ldmax] | vs [NR][ldmax] | full[NS] | empty[NS] | abort
-template <typename T>
+// Output a handled by consumer thread t, slot e: with two outputs per thread they
+// are adjacent (one 2-entry vector load per stored column), else one per thread.
+template <int CT, int NA> __device__ __forceinline__ int out_index(int t, int e) {
+  return NA == 2 ? 2 * t + e : t + CT * e;
+}
+
+// Two adjacent stored entries p[0], p[1] (16-byte aligned for float2 / 8 for half2).
+template <typename T, typename S> __device__ __forceinline__ void load_pair(const S *p, T &v0, T &v1) {
+  v0 = load_c<T>(p[0]);
+  v1 = load_c<T>(p[1]);
+}
+template <> __device__ __forceinline__ void load_pair<float2, float2>(const float2 *p, float2 &v0, float2 &v1) {
+  const float4 q = *reinterpret_cast<const float4 *>(p);
+  v0 = make_float2(q.x, q.y);
+  v1 = make_float2(q.z, q.w);
+}
+template <> __device__ __forceinline__ void load_pair<float2, __half2>(const __half2 *p, float2 &v0, float2 &v1) {
+  const uint2 q = *reinterpret_cast<const uint2 *>(p);
+  v0 = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
+  v1 = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+}
+
+// Shared memory layout: ring [NS][CH*ldmax] (stored type S) | vs [NR][ldmax] (compute type T) |
+// full[NS] | empty[NS] | abort
+template <typename T, typename S>
 __host__ __device__ inline size_t subst_smem(int ns, int ldmax, int nr) {
-  size_t stage = (size_t)chunk_cols<T>() * ldmax * sizeof(T);
+  size_t stage = (size_t)chunk_cols<S>() * ldmax * sizeof(S);
   size_t o = (size_t)ns * stage + (size_t)nr * ldmax * sizeof(T);
   o = (o + 15) & ~(size_t)15;
   return o + 2 * (size_t)ns * sizeof(uint64_t) + 16;
@@ -83,21 +109,21 @@ __host__ __device__ inline size_t subst_smem(int ns, int ldmax, int nr) {
 
 // One CTA per (box, group of NR right-hand sides): every factor block is read
 // once per group and applied to NR vectors.
-template <typename R, int CT, int NA, int NR>
+template <typename R, typename S, int CT, int NA, int NR>
 __global__ void __launch_bounds__(CT + 32)
-k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const C<R> *__restrict__ factor,
+k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const S *__restrict__ factor,
         const double2 *__restrict__ rg, int NX, int64_t vec_stride, C<R> *__restrict__ staging, int64_t stg_stride,
         int nrhs, int NS, int ldmax, int32_t *status) {
   using T = C<R>;
-  constexpr int CH = chunk_cols<T>();
+  constexpr int CH = chunk_cols<S>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const SubDev s = subs[blockIdx.x];
   const int m = s.ex, rows = s.ey, ldm = s.ldm;
   const int r0 = blockIdx.y * NR;
   const size_t stage_elems = (size_t)CH * ldmax;
-  T *ring = reinterpret_cast<T *>(smem_raw);
-  T *vs = ring + (size_t)NS * stage_elems;     // [NR][ldmax]
-  size_t off = ((size_t)NS * stage_elems + (size_t)NR * ldmax) * sizeof(T);
+  S *ring = reinterpret_cast<S *>(smem_raw);
+  T *vs = reinterpret_cast<T *>(ring + (size_t)NS * stage_elems);     // [NR][ldmax]
+  size_t off = (size_t)NS * stage_elems * sizeof(S) + (size_t)NR * ldmax * sizeof(T);
   off = (off + 15) & ~(size_t)15;
   uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + off);
   uint64_t *empty = full + NS;
@@ -116,7 +142,7 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
   const int nck = (m + CH - 1) / CH;             // chunks per factor block
   const int64_t total = (int64_t)(2 * rows - 1) * nck;
   const int64_t slot_elems = (int64_t)m * ldm;
-  const T *Fs = factor + s.foff;
+  const S *Fs = factor + s.foff;
 
   if (warp == CT / 32) {
     // ---------------- producer warp: stream the factor blocks in use order
@@ -130,7 +156,7 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
         const uint32_t ph = (uint32_t)((it / NS) & 1);
         if (!mbar_wait(&empty[slot], ph ^ 1u, abort_flag)) { ok = false; break; }
         const int cols = min(CH, m - c * CH);
-        const uint32_t bytes = (uint32_t)(cols * ldm * sizeof(T));
+        const uint32_t bytes = (uint32_t)(cols * ldm * sizeof(S));
         mbar_arrive_expect_tx(&full[slot], bytes);
         bulk_g2s(ring + (size_t)slot * stage_elems, Fs + j * slot_elems + (int64_t)c * CH * ldm, bytes, &full[slot]);
         issued = it + 1;
@@ -154,7 +180,7 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
   bool ownx[NA];
 #pragma unroll
   for (int e = 0; e < NA; ++e) {
-    const int a = tid + CT * e;
+    const int a = out_index<CT, NA>(tid, e);
     const int gx = s.ex0 + a;
     ownx[e] = a < m && gx >= s.ox0 && gx < s.ox1;
     const double2 t = a < m ? a1c[a] : make_double2(0, 0);
@@ -175,7 +201,7 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
       const T is = mk<T>((R)isd.x, (R)isd.y);
 #pragma unroll
       for (int e = 0; e < NA; ++e) {
-        const int a = tid + CT * e;
+        const int a = out_index<CT, NA>(tid, e);
         if (a < m) {
           const T la = cmul(a1[e], is);
 #pragma unroll
@@ -194,7 +220,7 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
       const T in = mk<T>((R)ind.x, (R)ind.y);
 #pragma unroll
       for (int e = 0; e < NA; ++e) {
-        const int a = tid + CT * e;
+        const int a = out_index<CT, NA>(tid, e);
         if (a < m) {
           const T ua = cmul(a1[e], in);
 #pragma unroll
@@ -215,17 +241,23 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
         *abort_flag = 1;
         atomicOr(status, ST_TIMEOUT);
       }
-      const T *blk = ring + (size_t)slot * stage_elems;
+      const S *blk = ring + (size_t)slot * stage_elems;
       const int b0 = c * CH;
       const int cols = min(CH, m - b0);
 #pragma unroll
       for (int b = 0; b < CH; ++b) {
         if (b < cols) {
           T sv[NA];
+          if (NA == 2) {
+            // entries 2t, 2t+1 of the column: one vector load (padding up to ldm is readable)
+            if (2 * tid < m) load_pair<T, S>(blk + b * ldm + 2 * tid, sv[0], sv[NA - 1]);
+            else { sv[0] = mk<T>(0, 0); sv[NA - 1] = mk<T>(0, 0); }
+          } else {
 #pragma unroll
-          for (int e = 0; e < NA; ++e) {
-            const int a = tid + CT * e;
-            sv[e] = a < m ? blk[b * ldm + a] : mk<T>(0, 0);
+            for (int e = 0; e < NA; ++e) {
+              const int a = out_index<CT, NA>(tid, e);
+              sv[e] = a < m ? load_c<T>(blk[b * ldm + a]) : mk<T>(0, 0);
+            }
           }
 #pragma unroll
           for (int q = 0; q < NR; ++q) {
@@ -244,7 +276,7 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
       T *stg = staging + (int64_t)(r0 + q) * stg_stride + s.soff;
 #pragma unroll
       for (int e = 0; e < NA; ++e) {
-        const int a = tid + CT * e;
+        const int a = out_index<CT, NA>(tid, e);
         if (a < m) {
           if (fwd) {
             w[e][q] = acc[e][q];
@@ -254,6 +286,244 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
             w[e][q] = x;
             stg[(int64_t)j * m + a] = x;
           }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Symmetric storage.  A is complex symmetric, so every S_j and S_j^{-1} is too,
+// and only the upper 16 x 16 tiles of S_j^{-1} are stored: tile (I, J), I <= J,
+// at position J(J+1)/2 + I, entry (r, c) of a tile at c*16 + ((r + c) & 15)
+// (the rotation keeps row- and column-wise reads free of bank conflicts).
+// This streams about (mt+1)/(2 mt) of the bytes of the full blocks.  A tile
+// (I, J) serves twice: y_I += T v_J and, off the diagonal, y_J += T^T v_I.
+// Tile-column J belongs to consumer warp min(J, mt-1-J) mod NW (pairing long
+// and short columns); in a warp, lane (rr, h) covers row / column rr of the
+// tile and half h of the 16 terms.  Column-wise sums stay in registers until
+// the column's diagonal tile; row-wise sums go to a per-warp partial vector in
+// shared memory; the step ends with y[a] = sum over warps of the partials.
+constexpr int TB = 16;
+
+template <typename S> __host__ __device__ constexpr int tiles_per_stage() {
+  return sizeof(S) == 16 ? 2 : (sizeof(S) == 8 ? 4 : 8);   // 8 KB stages
+}
+
+template <typename T, typename S>
+__host__ __device__ inline size_t subst_sym_smem(int ns, int mp, int nw, int nr, int nt) {
+  size_t o = (size_t)ns * tiles_per_stage<S>() * TB * TB * sizeof(S);
+  o += (size_t)nr * mp * sizeof(T) + (size_t)nw * nr * mp * sizeof(T);
+  o += 2 * (size_t)nt;
+  o = (o + 15) & ~(size_t)15;
+  return o + 2 * (size_t)ns * sizeof(uint64_t) + 16;
+}
+
+template <typename R, typename S, int NW, int NR>
+__global__ void __launch_bounds__(NW * 32 + 32)
+k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const S *__restrict__ factor,
+            const double2 *__restrict__ rg, int NX, int64_t vec_stride, C<R> *__restrict__ staging,
+            int64_t stg_stride, int nrhs, int NS, int mpmax, int32_t *status) {
+  using T = C<R>;
+  constexpr int CT = NW * 32;
+  constexpr int TPC = tiles_per_stage<S>();
+  constexpr int TE = TB * TB;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const SubDev s = subs[blockIdx.x];
+  const int m = s.ex, rows = s.ey;
+  const int mt = (m + TB - 1) / TB, mp = mt * TB, nt = mt * (mt + 1) / 2;
+  const int ntmax = (mpmax / TB) * (mpmax / TB + 1) / 2;
+  const int r0 = blockIdx.y * NR;
+  S *ring = reinterpret_cast<S *>(smem_raw);
+  T *vs = reinterpret_cast<T *>(ring + (size_t)NS * TPC * TE);   // [NR][mpmax]
+  T *part = vs + (size_t)NR * mpmax;                               // [NW][NR][mpmax]
+  uint8_t *tI = reinterpret_cast<uint8_t *>(part + (size_t)NW * NR * mpmax);
+  uint8_t *tJ = tI + ntmax;
+  size_t off = (size_t)NS * TPC * TE * sizeof(S) + (size_t)(NW + 1) * NR * mpmax * sizeof(T) + 2 * (size_t)ntmax;
+  off = (off + 15) & ~(size_t)15;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + off);
+  uint64_t *empty = full + NS;
+  volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + NS);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], NW);
+    }
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  for (int J = 0; J < mt; ++J)
+    for (int I = tid; I <= J; I += blockDim.x) {
+      tI[J * (J + 1) / 2 + I] = (uint8_t)I;
+      tJ[J * (J + 1) / 2 + I] = (uint8_t)J;
+    }
+  for (int i = tid; i < NW * NR * mpmax; i += blockDim.x) part[i] = mk<T>(0, 0);
+  __syncthreads();
+
+  const int nck = (nt + TPC - 1) / TPC;
+  const int64_t total = (int64_t)(2 * rows - 1) * nck;
+  const int64_t slot_elems = (int64_t)nt * TE;
+  const S *Fs = factor + s.foff;
+
+  if (warp == NW) {
+    // ---------------- producer warp: stream the tiles in use order
+    if (lane == 0) {
+      int64_t issued = 0;
+      bool ok = true;
+      for (int64_t it = 0; it < total && ok; ++it) {
+        const int st = (int)(it / nck), c = (int)(it - (int64_t)st * nck);
+        const int j = st < rows ? st : 2 * rows - 2 - st;
+        const int slot = (int)(it % NS);
+        const uint32_t ph = (uint32_t)((it / NS) & 1);
+        if (!mbar_wait(&empty[slot], ph ^ 1u, abort_flag)) { ok = false; break; }
+        const int ntile = min(TPC, nt - c * TPC);
+        const uint32_t bytes = (uint32_t)(ntile * TE * sizeof(S));
+        mbar_arrive_expect_tx(&full[slot], bytes);
+        bulk_g2s(ring + (size_t)slot * TPC * TE, Fs + j * slot_elems + (int64_t)c * TPC * TE, bytes, &full[slot]);
+        issued = it + 1;
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(status, ST_TIMEOUT);
+      }
+      for (int64_t it = max((int64_t)0, issued - NS); it < issued; ++it)
+        mbar_wait(&full[it % NS], (uint32_t)((it / NS) & 1), abort_flag);
+    }
+    return;
+  }
+
+  // ---------------- consumer warps (thread a owns output a of the step, a < mp)
+  const double2 *a1c = pool + s.aoff;
+  const double2 *a2c = a1c + 2 * m + 1;
+  const double2 *ia2f = a2c + rows;
+  const int a = tid;
+  const int gx = s.ex0 + a;
+  const bool ownx = a < m && gx >= s.ox0 && gx < s.ox1;
+  T a1 = mk<T>(0, 0);
+  if (a < m) {
+    const double2 t = a1c[a];
+    a1 = mk<T>((R)t.x, (R)t.y);
+  }
+  T w[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) w[q] = mk<T>(0, 0);
+  const int rr = lane & 15, h = lane >> 4;
+  int64_t it = 0;
+  bool ok = true;
+  for (int st = 0; st < 2 * rows - 1; ++st) {
+    const bool fwd = st < rows;
+    const int j = fwd ? st : 2 * rows - 2 - st;
+    consumer_sync(CT);   // the previous step's reads of vs are done
+    if (a < mp) {
+      if (fwd) {
+        const int gy = s.ey0 + j;
+        const bool owny = gy >= s.oy0 && gy < s.oy1;
+        const double2 isd = ia2f[j];
+        const T la = cmul(a1, mk<T>((R)isd.x, (R)isd.y));
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          T rho = mk<T>(0, 0);
+          if (owny && ownx && r0 + q < nrhs) {
+            const double2 rv = rg[(int64_t)(r0 + q) * vec_stride + (int64_t)gy * NX + gx];
+            rho = mk<T>((R)rv.x, (R)rv.y);
+          }
+          vs[q * mpmax + a] = a < m ? (j > 0 ? cfms(la, w[q], rho) : rho) : mk<T>(0, 0);
+        }
+      } else {
+        const double2 ind = ia2f[j + 1];
+        const T ua = cmul(a1, mk<T>((R)ind.x, (R)ind.y));
+#pragma unroll
+        for (int q = 0; q < NR; ++q) vs[q * mpmax + a] = a < m ? cmul(ua, w[q]) : mk<T>(0, 0);
+      }
+    }
+    consumer_sync(CT);
+    T accJ[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) accJ[q] = mk<T>(0, 0);
+    T *pw = part + (size_t)warp * NR * mpmax;
+    for (int c = 0; c < nck; ++c, ++it) {
+      const int slot = (int)(it % NS);
+      if (ok && !mbar_wait(&full[slot], (uint32_t)((it / NS) & 1), abort_flag)) {
+        ok = false;
+        *abort_flag = 1;
+        atomicOr(status, ST_TIMEOUT);
+      }
+      const S *stage = ring + (size_t)slot * TPC * TE;
+      const int u0 = c * TPC, un = min(TPC, nt - u0);
+      for (int du = 0; du < un; ++du) {
+        const int I = tI[u0 + du], J = tJ[u0 + du];
+        const int own = min(J, mt - 1 - J) % NW;
+        if (own != warp) continue;
+        const S *tile = stage + du * TE;
+        T pr[NR], pc[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) { pr[q] = mk<T>(0, 0); pc[q] = mk<T>(0, 0); }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int cc = 8 * h + k;
+          const T tv = load_c<T>(tile[cc * TB + ((rr + cc) & 15)]);   // T[rr][cc]
+#pragma unroll
+          for (int q = 0; q < NR; ++q) pr[q] = cfma(tv, vs[q * mpmax + J * TB + cc], pr[q]);
+        }
+        if (I != J) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int ai = 8 * h + k;
+            const T tv = load_c<T>(tile[rr * TB + ((ai + rr) & 15)]);  // T[ai][rr]
+#pragma unroll
+            for (int q = 0; q < NR; ++q) pc[q] = cfma(tv, vs[q * mpmax + I * TB + ai], pc[q]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          pr[q].x += __shfl_xor_sync(0xffffffffu, pr[q].x, 16);
+          pr[q].y += __shfl_xor_sync(0xffffffffu, pr[q].y, 16);
+          pc[q].x += __shfl_xor_sync(0xffffffffu, pc[q].x, 16);
+          pc[q].y += __shfl_xor_sync(0xffffffffu, pc[q].y, 16);
+          accJ[q] = cadd(accJ[q], pc[q]);
+        }
+        if (h == 0) {
+#pragma unroll
+          for (int q = 0; q < NR; ++q) {
+            T *dst = pw + q * mpmax + I * TB + rr;
+            *dst = cadd(*dst, pr[q]);
+            if (I == J) {   // the column is complete
+              T *dj = pw + q * mpmax + J * TB + rr;
+              *dj = cadd(*dj, accJ[q]);
+            }
+          }
+        }
+        if (I == J) {
+#pragma unroll
+          for (int q = 0; q < NR; ++q) accJ[q] = mk<T>(0, 0);
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+    }
+    consumer_sync(CT);   // every warp's partial sums are in shared memory
+    if (a < m) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        T y = mk<T>(0, 0);
+        for (int ww = 0; ww < NW; ++ww) {
+          T *p = part + ((size_t)ww * NR + q) * mpmax + a;
+          y = cadd(y, *p);
+          *p = mk<T>(0, 0);
+        }
+        if (r0 + q < nrhs) {
+          T *stg = staging + (int64_t)(r0 + q) * stg_stride + s.soff;
+          if (fwd) {
+            w[q] = y;
+            stg[(int64_t)j * m + a] = y;
+          } else {
+            const T x = csub(stg[(int64_t)j * m + a], y);
+            w[q] = x;
+            stg[(int64_t)j * m + a] = x;
+          }
+        } else {
+          w[q] = y;
         }
       }
     }
@@ -290,14 +560,14 @@ k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const
 }
 
 // Ring depth: as deep as shared memory allows for the CTAs that share an SM.
-template <typename T>
+template <typename T, typename S>
 static int ring_stages(const hd_ctx *ctx, int ldmax, int nr, int groups) {
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ctas = (int64_t)ctx->nsub * groups;
   const int per_sm = (int)std::min<int64_t>(7, (ctas + sms - 1) / sms);
   const size_t budget = (size_t)200 * 1024 / (size_t)std::max(1, per_sm);
-  const size_t stage = (size_t)chunk_cols<T>() * ldmax * sizeof(T);
+  const size_t stage = (size_t)chunk_cols<S>() * ldmax * sizeof(S);
   const size_t fixed = (size_t)nr * ldmax * sizeof(T) + 64;
   int ns = budget > fixed ? (int)((budget - fixed) / stage) : 2;
   return std::min(32, std::max(2, ns));
@@ -306,53 +576,103 @@ static int ring_stages(const hd_ctx *ctx, int ldmax, int nr, int groups) {
 // Right-hand sides per CTA: one factor read serves NR vectors.
 static int rhs_per_cta(int nrhs) { return nrhs >= 8 ? 8 : (nrhs >= 4 ? 4 : (nrhs >= 2 ? 2 : 1)); }
 
-size_t subst_ring_bytes(const hd_ctx *ctx, int *stages) {
-  const int ldmax = (ctx->max_m + 1) & ~1;
-  if (ctx->prec == HD_C64) {
-    int ns = ring_stages<float2>(ctx, ldmax, 1, 1);
-    if (stages) *stages = ns;
-    return subst_smem<float2>(ns, ldmax, 1);
-  }
-  int ns = ring_stages<double2>(ctx, ldmax, 1, 1);
-  if (stages) *stages = ns;
-  return subst_smem<double2>(ns, ldmax, 1);
-}
+static int ld_max(const hd_ctx *ctx) { return (ctx->max_m + 3) & ~3; }
 
-template <typename R, int CT, int NR>
+template <typename R, typename S, int CT, int NR>
 static cudaError_t launch_subst(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec_stride, void *staging,
                                 int64_t stg_stride, cudaStream_t st) {
+  constexpr int NA = CT >= 192 ? 1 : 2;   // outputs per consumer thread
   using T = C<R>;
-  const int ldmax = (ctx->max_m + 1) & ~1;
+  const int ldmax = ld_max(ctx);
   const int groups = (nrhs + NR - 1) / NR;
-  const int ns = ring_stages<T>(ctx, ldmax, NR, groups);
-  const size_t smem = subst_smem<T>(ns, ldmax, NR);
-  cudaError_t e = cudaFuncSetAttribute(k_subst<R, CT, 2, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int ns = (NR == 1 && ctx->tune_ns > 0) ? ctx->tune_ns : ring_stages<T, S>(ctx, ldmax, NR, groups);
+  const size_t smem = subst_smem<T, S>(ns, ldmax, NR);
+  cudaError_t e = cudaFuncSetAttribute(k_subst<R, S, CT, NA, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid(ctx->nsub, groups);
-  k_subst<R, CT, 2, NR><<<grid, CT + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,
-                                                     reinterpret_cast<const T *>(ctx->factor), r, ctx->NX, vec_stride,
-                                                     reinterpret_cast<T *>(staging), stg_stride, nrhs, ns, ldmax,
-                                                     ctx->d_status);
+  k_subst<R, S, CT, NA, NR><<<grid, CT + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,
+                                                        reinterpret_cast<const S *>(ctx->factor), r, ctx->NX,
+                                                        vec_stride, reinterpret_cast<T *>(staging), stg_stride, nrhs,
+                                                        ns, ldmax, ctx->d_status);
   return cudaGetLastError();
 }
 
-template <typename R, int CT>
+template <typename R, typename S, int CT>
 static cudaError_t launch_subst_nr(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vs, void *stg, int64_t ss,
                                    cudaStream_t st) {
   switch (rhs_per_cta(nrhs)) {
-    case 8: return launch_subst<R, CT, 8>(ctx, r, nrhs, vs, stg, ss, st);
-    case 4: return launch_subst<R, CT, 4>(ctx, r, nrhs, vs, stg, ss, st);
-    case 2: return launch_subst<R, CT, 2>(ctx, r, nrhs, vs, stg, ss, st);
-    default: return launch_subst<R, CT, 1>(ctx, r, nrhs, vs, stg, ss, st);
+    case 8: return launch_subst<R, S, CT, 8>(ctx, r, nrhs, vs, stg, ss, st);
+    case 4: return launch_subst<R, S, CT, 4>(ctx, r, nrhs, vs, stg, ss, st);
+    case 2: return launch_subst<R, S, CT, 2>(ctx, r, nrhs, vs, stg, ss, st);
+    default: return launch_subst<R, S, CT, 1>(ctx, r, nrhs, vs, stg, ss, st);
   }
 }
 
-template <typename R>
+template <typename R, typename S, int NW, int NR>
+static cudaError_t launch_subst_sym(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec_stride, void *staging,
+                                    int64_t stg_stride, cudaStream_t st) {
+  using T = C<R>;
+  const int mpmax = (ctx->max_m + TB - 1) / TB * TB;
+  const int ntmax = (mpmax / TB) * (mpmax / TB + 1) / 2;
+  const int groups = (nrhs + NR - 1) / NR;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = (int)std::min<int64_t>(7, ((int64_t)ctx->nsub * groups + sms - 1) / sms);
+  const size_t fixed = subst_sym_smem<T, S>(0, mpmax, NW, NR, ntmax);
+  const size_t stage = (size_t)tiles_per_stage<S>() * TB * TB * sizeof(S);
+  const size_t budget = (size_t)200 * 1024 / (size_t)std::max(1, per_sm);
+  int ns = ctx->tune_ns > 0 && NR == 1 ? ctx->tune_ns : (budget > fixed ? (int)((budget - fixed) / (stage + 16)) : 2);
+  ns = std::min(32, std::max(2, ns));
+  const size_t smem = subst_sym_smem<T, S>(ns, mpmax, NW, NR, ntmax);
+  cudaError_t e = cudaFuncSetAttribute(k_subst_sym<R, S, NW, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(ctx->nsub, groups);
+  k_subst_sym<R, S, NW, NR><<<grid, NW * 32 + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,
+                                                              reinterpret_cast<const S *>(ctx->factor), r, ctx->NX,
+                                                              vec_stride, reinterpret_cast<T *>(staging), stg_stride,
+                                                              nrhs, ns, mpmax, ctx->d_status);
+  return cudaGetLastError();
+}
+
+template <typename R, typename S, int NW>
+static cudaError_t launch_subst_sym_nr(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vs, void *stg, int64_t ss,
+                                       cudaStream_t st) {
+  switch (rhs_per_cta(nrhs)) {
+    case 8: return launch_subst_sym<R, S, NW, 8>(ctx, r, nrhs, vs, stg, ss, st);
+    case 4: return launch_subst_sym<R, S, NW, 4>(ctx, r, nrhs, vs, stg, ss, st);
+    case 2: return launch_subst_sym<R, S, NW, 2>(ctx, r, nrhs, vs, stg, ss, st);
+    default: return launch_subst_sym<R, S, NW, 1>(ctx, r, nrhs, vs, stg, ss, st);
+  }
+}
+
+template <typename R, typename S>
 static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs,
                                   void *staging, cudaStream_t st) {
+  if (ctx->sym) {
+    tic(ctx, T_SUBST, st);
+    cudaError_t e = ctx->max_m <= 192 ? launch_subst_sym_nr<R, S, 6>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
+                                      : launch_subst_sym_nr<R, S, 8>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st);
+    toc(ctx, T_SUBST, st, 1);
+    if (e != cudaSuccess) return e;
+    dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
+    tic(ctx, T_GATHER, st);
+    k_gather<R><<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
+                                      ctx->nby, reinterpret_cast<const C<R> *>(staging), ctx->staging_elems, z, zs,
+                                      ctx->NX);
+    toc(ctx, T_GATHER, st, 1);
+    return cudaGetLastError();
+  }
   tic(ctx, T_SUBST, st);
-  cudaError_t e = ctx->max_m <= 192 ? launch_subst_nr<R, 96>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
-                                    : launch_subst_nr<R, 128>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st);
+  // consumer threads: 96 or 192 cover boxes up to 192 wide, 128 or 256 up to 256
+  int ct = ctx->tune_ct ? ctx->tune_ct : (ctx->max_m <= 192 ? 96 : 128);
+  if (ct == 96 || ct == 192) ct = ctx->max_m <= 192 ? ct : (ct == 96 ? 128 : 256);
+  cudaError_t e;
+  switch (ct) {
+    case 96: e = launch_subst_nr<R, S, 96>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st); break;
+    case 192: e = launch_subst_nr<R, S, 192>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st); break;
+    case 256: e = launch_subst_nr<R, S, 256>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st); break;
+    default: e = launch_subst_nr<R, S, 128>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st); break;
+  }
   toc(ctx, T_SUBST, st, 1);
   if (e != cudaSuccess) return e;
   dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
@@ -366,9 +686,94 @@ static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, dou
 
 int run_apply(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs, void *staging,
               cudaStream_t st) {
-  cudaError_t e = ctx->prec == HD_C64 ? launch_apply_r<float>(ctx, r, rs, z, zs, nrhs, staging, st)
-                                      : launch_apply_r<double>(ctx, r, rs, z, zs, nrhs, staging, st);
+  cudaError_t e = ctx->prec == HD_C64    ? launch_apply_r<float, float2>(ctx, r, rs, z, zs, nrhs, staging, st)
+                  : ctx->prec == HD_C64_H ? launch_apply_r<float, __half2>(ctx, r, rs, z, zs, nrhs, staging, st)
+                                          : launch_apply_r<double, double2>(ctx, r, rs, z, zs, nrhs, staging, st);
   if (e != cudaSuccess) return cuda_fail(e, "preconditioner launch");
+  return HD_OK;
+}
+
+}  // namespace hd
+
+// ---------------------------------------------------------------------------
+// Autotuner of the substitution launch: consumer threads per CTA (96 or 128)
+// and ring depth, timed with CUDA events on real applications; the winner is
+// remembered per (precision, widest box, boxes, device) for the process.
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace hd {
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st, int *ct_out,
+                   int *ns_out, float *ms_out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(ctx->prec, ctx->sym ? 1 : 0, ctx->max_m, ctx->nsub, dev);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      ctx->tune_ct = it->second.first;
+      ctx->tune_ns = it->second.second;
+      if (ct_out) *ct_out = ctx->tune_ct;
+      if (ns_out) *ns_out = ctx->tune_ns;
+      if (ms_out) *ms_out = -1.f;
+      return HD_OK;
+    }
+  }
+  const int ldmax = ld_max(ctx);
+  // one ring stage: 8 KB of tiles (symmetric) or chunk_cols<S>() columns of ldmax entries (64 bytes per row)
+  const size_t stage = ctx->sym ? (size_t)8192 : (size_t)ldmax * 64;
+  int dev_optin = 0;
+  cudaDeviceGetAttribute(&dev_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  std::vector<int> cts = ctx->sym ? std::vector<int>{ctx->max_m <= 192 ? 192 : 256}
+                                  : (ctx->max_m <= 192 ? std::vector<int>{96, 128, 192} : std::vector<int>{128, 256});
+  const int ns_list[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int best_ct = 0, best_ns = 0;
+  const bool prof = ctx->profiling;
+  ctx->profiling = false;
+  for (int ct : cts)
+    for (int ns : ns_list) {
+      if ((size_t)ns * stage + (ctx->sym ? 24576 : 8192) > (size_t)std::min(dev_optin, 224 * 1024)) continue;
+      ctx->tune_ct = ct;
+      ctx->tune_ns = ns;
+      float tot = 0.f;
+      bool ok = true;
+      for (int rep = 0; rep < 3 && ok; ++rep) {
+        cudaEventRecord(e0, st);
+        ok = run_apply(ctx, r, 0, z, 0, 1, staging, st) == HD_OK;
+        if (!ok) cudaGetLastError();   // a shape that does not fit leaves no error behind
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) tot += ms;   // the first run warms up
+      }
+      if (ok && tot < best) { best = tot; best_ct = ct; best_ns = ns; }
+    }
+  ctx->profiling = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->t_launch[T_SUBST] = 0;
+  ctx->t_launch[T_GATHER] = 0;
+  if (!best_ct) { set_error("hd_autotune: no substitution configuration ran"); return HD_ERR_CUDA; }
+  ctx->tune_ct = best_ct;
+  ctx->tune_ns = best_ns;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {best_ct, best_ns};
+  }
+  if (ct_out) *ct_out = best_ct;
+  if (ns_out) *ns_out = best_ns;
+  if (ms_out) *ms_out = best / 2.f;
   return HD_OK;
 }
 

@@ -26,17 +26,19 @@ class HelmholtzDDM:
     def __init__(self, N: int, npml: int, omega: float, c, nbx: int, nby: int, overlap: int,
                  precision: str = "c64", cut_x: Optional[Sequence[int]] = None, cut_y: Optional[Sequence[int]] = None,
                  own_global_pml: bool = True, sigma0_over_omega: float = 20.0, pml_power: int = 2,
-                 device: str = "cuda", stream: Optional[torch.cuda.Stream] = None, factor: bool = True):
+                 device: str = "cuda", stream: Optional[torch.cuda.Stream] = None, factor: bool = True,
+                 symmetric: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("HelmholtzDDM needs a CUDA device: there is no CPU path")
         self.N, self.npml, self.n = N, npml, N + 2 * npml
         self.device = torch.device(device)
         self.stream = stream
-        self.prec = {"c64": B.HD_C64, "c128": B.HD_C128}[precision]
+        self.prec = {"c64": B.HD_C64, "c64h": B.HD_C64_H, "c128": B.HD_C128}[precision]
         c_t = torch.as_tensor(np.asarray(c, dtype=np.float64) if not torch.is_tensor(c) else c,
                               dtype=torch.float64).to(self.device).contiguous()
         assert c_t.shape == (self.n, self.n), f"velocity must be {(self.n, self.n)}"
-        self.ctx = B.hd_setup_medium(N, N, npml, 1.0 / N, omega, c_t.data_ptr(), self.prec, self._st(),
+        self.ctx = B.hd_setup_medium(N, N, npml, 1.0 / N, omega, c_t.data_ptr(),
+                                     self.prec | (B.HD_SYMMETRIC if symmetric else 0), self._st(),
                                      nbx, nby, overlap, cut_x, cut_y, int(own_global_pml), sigma0_over_omega,
                                      pml_power)
         fb, _, sb = B.hd_query_workspace(self.ctx, 1, 1)
@@ -55,6 +57,13 @@ class HelmholtzDDM:
         B.hd_factor_subdomains(self.ctx, self.factor_buf.data_ptr(), self.factor_bytes, self.scratch.data_ptr(),
                                self.scratch_bytes, self._st())
         self.factored = True
+
+    def autotune(self):
+        """Picks the substitution launch shape by timing (cached per shape for the process)."""
+        r = torch.zeros((self.n, self.n), dtype=torch.complex128, device=self.device)
+        z = torch.empty_like(r)
+        return B.hd_autotune(self.ctx, r.data_ptr(), z.data_ptr(), self.scratch.data_ptr(), self.scratch_bytes,
+                             self._st())
 
     def _vec(self, x):
         x = torch.as_tensor(x, dtype=torch.complex128, device=self.device).contiguous()
@@ -93,9 +102,9 @@ class HelmholtzDDM:
         return self._krylov[key]
 
     def solve(self, b, restart: int = 50, rtol: float = 1e-8, max_iters: int = 1000, x0=None, out=None,
-              arnoldi: str = "auto"):
+              arnoldi: str = "auto", graphs: bool = False):
         """FGMRES solve of A x = b.  ``arnoldi``: "fp64", "ds" (double-single
-        Gram-Schmidt on the FP32 pipes) or "auto" (ds with c64 factors, fp64 with c128)."""
+        Gram-Schmidt on the FP32 pipes) or "auto" (ds with FP32 factors, fp64 with c128)."""
         b, nrhs = self._vec(b)
         if out is not None:
             x = out
@@ -106,12 +115,13 @@ class HelmholtzDDM:
         kws = self.krylov_workspace(restart, nrhs)
         rc, stats = B.hd_gmres_solve(self.ctx, b.data_ptr(), x.data_ptr(), nrhs, restart, max_iters, rtol,
                                      kws.data_ptr(), kws.numel(), self.scratch.data_ptr(), self.scratch_bytes,
-                                     self._st(), use_x0=int(x0 is not None), arnoldi=self._arnoldi(arnoldi))
+                                     self._st(), use_x0=int(x0 is not None), arnoldi=self._arnoldi(arnoldi),
+                                     graphs=int(graphs))
         return x, stats
 
     def _arnoldi(self, mode: str) -> int:
         if mode == "auto":
-            mode = "ds" if self.prec == B.HD_C64 else "fp64"
+            mode = "ds" if self.prec != B.HD_C128 else "fp64"
         return {"fp64": B.HD_ARNOLDI_FP64, "ds": B.HD_ARNOLDI_DS}[mode]
 
     def set_profiling(self, on: bool = True):
@@ -134,7 +144,7 @@ class HelmholtzDDM:
 
 def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: int, overlap: int,
                restart: int, rtol: float, max_iters: int = 5000, precision: str = "c64", cut_x=None, cut_y=None,
-               device: str = "cuda", arnoldi: str = "auto"):
+               device: str = "cuda", arnoldi: str = "auto", symmetric: bool = False):
     """End-to-end solve from host arrays: velocity c [n][n] (float64) and source
     samples f [nrhs][n][n] (complex128), preferably in pinned memory.  Copies in,
     sets up the medium, factorises, forms b = J h^2 f, runs FGMRES and copies the
@@ -143,7 +153,7 @@ def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: i
     c_d = torch.as_tensor(c_host).to(dev, non_blocking=True)
     f_d = torch.as_tensor(f_host).to(dev, non_blocking=True)
     s = HelmholtzDDM(N, npml, omega, c_d, nbx, nby, overlap, precision=precision, cut_x=cut_x, cut_y=cut_y,
-                     device=device)
+                     device=device, symmetric=symmetric)
     b = s.rhs(f_d)
     x, stats = s.solve(b, restart=restart, rtol=rtol, max_iters=max_iters, arnoldi=arnoldi)
     x_h = x.to("cpu")
@@ -161,16 +171,17 @@ class Server:
         self._keep = {}
 
     def submit(self, c, f, N, npml, omega, nbx, nby, overlap, restart, rtol, max_iters=5000, precision="c64",
-               cut_x=None, cut_y=None, arnoldi="auto"):
+               cut_x=None, cut_y=None, arnoldi="auto", symmetric=False):
         """c: float64 [n][n], f: complex128 [nrhs][n][n] host arrays.  Returns a ticket."""
         c = np.ascontiguousarray(c, dtype=np.float64)
         f = np.ascontiguousarray(f, dtype=np.complex128)
         if f.ndim == 2:
             f = f[None]
         x = np.empty_like(f)
-        prec = {"c64": B.HD_C64, "c128": B.HD_C128}[precision]
-        mode = arnoldi if arnoldi != "auto" else ("ds" if prec == B.HD_C64 else "fp64")
-        t = B.hd_submit(self.srv, N, N, npml, 1.0 / N, omega, c.ctypes.data, f.ctypes.data, f.shape[0], prec,
+        prec = {"c64": B.HD_C64, "c64h": B.HD_C64_H, "c128": B.HD_C128}[precision]
+        mode = arnoldi if arnoldi != "auto" else ("ds" if prec != B.HD_C128 else "fp64")
+        t = B.hd_submit(self.srv, N, N, npml, 1.0 / N, omega, c.ctypes.data, f.ctypes.data, f.shape[0],
+                        prec | (B.HD_SYMMETRIC if symmetric else 0),
                         restart, max_iters, rtol, x.ctypes.data, nbx, nby, overlap, cut_x, cut_y,
                         arnoldi={"fp64": B.HD_ARNOLDI_FP64, "ds": B.HD_ARNOLDI_DS}[mode])
         self._keep[t] = (c, f, x)

@@ -49,9 +49,12 @@ def oracle(name, own=True):
 
 
 def gpu(name, precision, own=True):
+    """precision: c128 / c64 / c64h, with a trailing "s" for symmetric tile storage."""
     case, c, g, _, _ = oracle(name, own)
+    sym = precision.endswith("s")
     return HelmholtzDDM(case["N"], case["npml"], g.omega, c, case["nb"], case["nb"], case["overlap"],
-                        precision=precision, cut_x=cuts(case), cut_y=cuts(case), own_global_pml=own)
+                        precision=precision.rstrip("s"), cut_x=cuts(case), cut_y=cuts(case), own_global_pml=own,
+                        symmetric=sym)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -69,7 +72,8 @@ def test_matvec_and_rhs(name):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4)])
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4), ("c64h", 3e-2), ("c128s", 1e-10),
+                                           ("c64s", 2e-4), ("c64hs", 3e-2)])
 def test_precond_parity(name, precision, tol):
     _, _, g, _, P = oracle(name)
     s = gpu(name, precision)
@@ -122,11 +126,13 @@ def test_gmres_converged_c128(name, arnoldi):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-def test_gmres_mixed_precision(name):
-    """c64 local factors, FP64 outer loop: FP64 relative residual reaches the
-    tolerance and the solution matches the FP64 oracle to 1e-5."""
+@pytest.mark.parametrize("precision", ["c64", "c64h", "c64s"])
+def test_gmres_mixed_precision(name, precision):
+    """FP32 local factors (stored in FP32 or FP16), FP64 outer loop: the FP64
+    relative residual reaches the tolerance and the solution matches the FP64
+    oracle to 1e-5."""
     case, c, g, A, P = oracle(name)
-    s = gpu(name, "c64")
+    s = gpu(name, precision)
     f = W.gaussian_source(case["N"], case["npml"], 0.5, 0.5, 2.0 / case["N"])
     b = rhs_from_source(g, f)
     ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=50, rtol=1e-10, max_iters=400)
@@ -159,7 +165,7 @@ def _sources(case, k, seed):
     return np.stack([W.gaussian_source(N, npml, *rng.uniform(0.15, 0.85, 2), 2.0 / N) for _ in range(k)])
 
 
-@pytest.mark.parametrize("precision,nrhs", [("c128", 3), ("c64", 9)])
+@pytest.mark.parametrize("precision,nrhs", [("c128", 3), ("c64", 9), ("c64s", 5)])
 def test_precond_batched_equals_single(precision, nrhs):
     """Each right-hand side of a batched application (groups of up to 8 per CTA)
     gives bitwise the same vector as its own application."""
@@ -174,7 +180,7 @@ def test_precond_batched_equals_single(precision, nrhs):
     for k in range(nrhs):
         zk = s.apply_precond(torch.from_numpy(r[k])).cpu().numpy()
         assert np.array_equal(z[k], zk)
-    tol = 1e-10 if precision == "c128" else 2e-4
+    tol = 1e-10 if precision.startswith("c128") else 2e-4
     assert rel(z[nrhs - 1], P.apply(r[nrhs - 1])) < tol
 
 
@@ -195,3 +201,30 @@ def test_gmres_batched_alone_vs_mix(precision):
         assert np.linalg.norm(b[k].ravel() - A @ xb[k].ravel()) / np.linalg.norm(b[k]) <= 1e-8
     ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b[1], restart=20, rtol=1e-10, max_iters=400)
     assert rel(xb[1].ravel(), ref.x) < (1e-7 if precision == "c128" else 1e-5)
+
+
+def test_autotune_keeps_results():
+    """The autotuner only changes the launch shape: results stay bitwise identical."""
+    _, _, g, _, P = oracle("layers4")
+    s = gpu("layers4", "c64")
+    r = W.random_complex((g.n, g.n), seed=31)
+    z0 = s.apply_precond(torch.from_numpy(r)).cpu().numpy()
+    threads, stages, ms = s.autotune()
+    assert threads in (96, 128, 192, 256) and 2 <= stages <= 32
+    z1 = s.apply_precond(torch.from_numpy(r)).cpu().numpy()
+    assert np.array_equal(z0, z1)
+
+
+@pytest.mark.parametrize("precision", ["c128", "c64"])
+def test_gmres_graph_capture_matches_launches(precision):
+    """Arnoldi steps captured once as CUDA graphs and replayed (second solve on the
+    same workspace) give bitwise the solution of plain launches."""
+    case, c, g, A, P = oracle("ragged")
+    s = gpu("ragged", precision)
+    b = rhs_from_source(g, W.gaussian_source(case["N"], case["npml"], 0.35, 0.6, 2.0 / case["N"]))
+    x0, st0 = s.solve(torch.from_numpy(b), restart=10, rtol=1e-9, max_iters=200)
+    x1, st1 = s.solve(torch.from_numpy(b), restart=10, rtol=1e-9, max_iters=200, graphs=True)
+    x2, st2 = s.solve(torch.from_numpy(b), restart=10, rtol=1e-9, max_iters=200, graphs=True)
+    assert st0[0]["iters"] == st1[0]["iters"] == st2[0]["iters"] and st2[0]["converged"] == 1
+    assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
+    assert np.array_equal(x0.cpu().numpy(), x2.cpu().numpy())
