@@ -63,6 +63,9 @@ def parse():
     p.add_argument("--arnoldi", default="auto", choices=("auto", "fp64", "ds"))
     p.add_argument("--no-autotune", dest="autotune", action="store_false")
     p.add_argument("--symmetric", action="store_true", help="store only the upper tiles of each S_j^{-1}")
+    p.add_argument("--overlap", type=int, default=None, help="extra overlap lo in cells (default 8)")
+    p.add_argument("--probe-peaks", action="store_true", help="also measure FP64/FP32 FMA and copy rates")
+    p.add_argument("--npml", type=int, default=None, help="PML cells per side (default 16)")
     p.add_argument("--nrhs", type=int, default=None, help="sources per solve (batching config: 64)")
     p.add_argument("--group", type=int, default=16, help="sources solved together in lockstep")
     p.add_argument("--single-sample", type=int, default=2, help="batching: sources also solved one at a time")
@@ -168,7 +171,9 @@ class Clocks:
 # ----------------------------------------------------------------------------- workload
 def workload(args, rank: int):
     nrhs = args.nrhs or (64 if args.config == "batching" else 1)
-    wl = W.make_workload(args.config, restart=args.restart, rtol=args.rtol, nrhs=nrhs)
+    extra = {k: v for k, v in (("overlap", getattr(args, "overlap", None)), ("npml", getattr(args, "npml", None)))
+             if v is not None}
+    wl = W.make_workload(args.config, restart=args.restart, rtol=args.rtol, nrhs=nrhs, **extra)
     if rank > 0:  # every rank solves its own problem: same medium, its own source position
         rng = np.random.Generator(np.random.PCG64(7919 * rank + 17))
         xs, ys = rng.uniform(0.05, 0.95, size=2)
@@ -399,6 +404,13 @@ def run_ours(args, world, rank, local):
         out["e2e"] = {"value": world * args.e2e_steps / te, "unit": "solves/s", "h2d_bytes_per_step": h2d,
                       "d2h_bytes_per_step": d2h, "steps": args.e2e_steps}
 
+    if args.probe_peaks:
+        from paper_1508_02897_gb300 import _binding as B
+        buf = torch.empty(4 << 30, dtype=torch.uint8, device=dev)
+        f64, f32, cp = B.hd_probe_peaks(buf.data_ptr(), buf.numel(), int(stream.cuda_stream))
+        out["probed_peaks"] = {"fp64_tflops": f64, "fp32_tflops": f32, "copy_gbs": cp}
+        del buf
+
     if rank == 0 and not args.no_cpu_baseline:
         it_ref = int(round(statistics.mean(iters)))
         out["cpu_baseline"] = cpu_baseline(wl, it_ref, args.cpu_sample_boxes, "GPU FGMRES iteration count",
@@ -441,7 +453,7 @@ def _profile_traffic(wl, args):
         return None
 
 
-KERNEL_REV = "subst-v1"
+KERNEL_REV = "subst-v3"
 
 
 # ----------------------------------------------------------------------------- serving

@@ -224,6 +224,14 @@ int hd_gmres_solve(hd_ctx *ctx, const void *b_dev, void *x_dev, int32_t nrhs, co
 int hd_autotune(hd_ctx *ctx, const void *r_dev, void *z_dev, void *scratch_dev, size_t scratch_bytes,
                 int32_t *threads_out, int32_t *stages_out, float *ms_out, void *stream);
 
+/* Roofline denominators measured on the current device (no counterpart in the
+ * paper): FP64 and FP32 FMA throughput (TFLOP/s, eight independent FMA chains
+ * per thread) and a device-to-device copy through buf_dev (GB/s counting bytes
+ * read plus written).  buf_dev: at least 64 MiB of scratch (1 GiB or more gives
+ * a copy larger than L2).  Synchronises `stream`.  Outputs may be NULL. */
+int hd_probe_peaks(void *buf_dev, size_t buf_bytes, double *fp64_tflops, double *fp32_tflops, double *copy_gbs,
+                   void *stream);
+
 /* Per-kernel-class timing with CUDA events recorded on the launching stream
  * (events only while profiling is on; off by default).  Classes: 0
  * factorisation, 1 restrict + forward/back substitution, 2 gather-sum,

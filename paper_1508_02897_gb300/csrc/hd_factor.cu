@@ -30,7 +30,7 @@
 
 namespace hd {
 
-constexpr int FT = 512;        // threads per CTA
+constexpr int FT = 256;        // threads per CTA (two CTAs, two boxes, share an SM)
 constexpr int PB = 16;         // panel width
 constexpr int TR = 4, TC = 4;  // GEMM tile of the trailing update (rows x columns)
 
@@ -68,7 +68,7 @@ __device__ __forceinline__ T d_entry(int r, int c, int j, const double2 *a1c, co
 }
 
 template <typename R, typename S, bool SYM>
-__global__ void __launch_bounds__(FT, 1)
+__global__ void __launch_bounds__(FT, 2)
 k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const double *__restrict__ k2, int NX,
          double h2, S *__restrict__ factor, C<R> *__restrict__ work, int32_t *status) {
   using T = C<R>;

@@ -151,15 +151,15 @@ __global__ void __launch_bounds__(DT) k_update(const double2 *__restrict__ V, in
   }
 }
 
-// v_r = w_r / sqrt(red[4 r].x) (a squared norm); grid (.., nrhs).
+// v_r = w_r * red[4 r + 1].x, the reciprocal norm left there by k_cycle_init /
+// k_arnoldi_step (one FP64 division per right-hand side, not per entry); grid (.., nrhs).
 __global__ void __launch_bounds__(256) k_scale(const double2 *__restrict__ w_all, int64_t ldw,
                                                const double2 *__restrict__ red, double2 *__restrict__ v_all,
                                                int64_t ldvr, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int r = blockIdx.y;
-  double s = sqrt(red[4 * r].x);
-  double inv = s > 0.0 ? 1.0 / s : 0.0;
+  const double inv = red[4 * r + 1].x;
   double2 a = w_all[(int64_t)r * ldw + i];
   v_all[(int64_t)r * ldvr + i] = make_double2(a.x * inv, a.y * inv);
 }
@@ -333,15 +333,14 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
   }
 }
 
-// v_r = w_r / sqrt(red[4 r].x) written twice: split into V (double-single) and FP64 into vin.
+// v_r = w_r * red[4 r + 1].x written twice: split into V (double-single) and FP64 into vin.
 __global__ void __launch_bounds__(256) k_scale_df(const double2 *__restrict__ w_all, int64_t ldw,
                                                   const double2 *__restrict__ red, float4 *__restrict__ vout_all,
                                                   int64_t ldvr, double2 *__restrict__ vin_all, int64_t n) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int r = blockIdx.y;
-  double s = sqrt(red[4 * r].x);
-  double inv = s > 0.0 ? 1.0 / s : 0.0;
+  const double inv = red[4 * r + 1].x;
   double2 a = w_all[(int64_t)r * ldw + i];
   double2 v = make_double2(a.x * inv, a.y * inv);
   float2 cr = split_d(v.x), ci = split_d(v.y);
@@ -368,10 +367,13 @@ __device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, a.y); }
 
 __global__ void k_cycle_init(GmresDev d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= d.nrhs || !d.live[r]) return;
+  if (r >= d.nrhs) return;
+  const double beta = sqrt(d.red[4 * r].x);
+  d.red[4 * r + 1] = make_double2(beta > 0.0 ? 1.0 / beta : 0.0, 0.0);
+  if (!d.live[r]) return;
   double2 *g = d.g + (int64_t)r * d.ldh;
   for (int i = 0; i < d.ldh; ++i) g[i] = make_double2(0.0, 0.0);
-  g[0] = make_double2(sqrt(d.red[4 * r].x), 0.0);
+  g[0] = make_double2(beta, 0.0);
 }
 
 // Column j of H from the two CGS passes, old rotations, new rotation, g update.
@@ -381,6 +383,10 @@ __global__ void k_arnoldi_step(GmresDev d, int j) {
   double2 *Hj = d.H + ((int64_t)r * d.restart + j) * d.ldh;
   const double2 *h1 = d.h1 + (int64_t)r * d.ldh, *h2 = d.h2 + (int64_t)r * d.ldh;
   double *cs = d.cs + (int64_t)r * d.restart;
+  {
+    const double nrm = sqrt(d.red[4 * r].x);
+    d.red[4 * r + 1] = make_double2(nrm > 0.0 ? 1.0 / nrm : 0.0, 0.0);   // for k_scale
+  }
   double2 *sn = d.sn + (int64_t)r * d.restart;
   double2 *g = d.g + (int64_t)r * d.ldh;
   for (int i = 0; i <= j; ++i) Hj[i] = cadd(h1[i], h2[i]);

@@ -301,7 +301,7 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
 // (I, J) serves twice: y_I += T v_J and, off the diagonal, y_J += T^T v_I.
 // Tile-column J belongs to consumer warp min(J, mt-1-J) mod NW (pairing long
 // and short columns); in a warp, lane (rr, h) covers row / column rr of the
-// tile and half h of the 16 terms.  Column-wise sums stay in registers until
+// tile and the terms of parity h.  Column-wise sums stay in registers until
 // the column's diagonal tile; row-wise sums go to a per-warp partial vector in
 // shared memory; the step ends with y[a] = sum over warps of the partials.
 constexpr int TB = 16;
@@ -461,7 +461,7 @@ k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, c
         for (int q = 0; q < NR; ++q) { pr[q] = mk<T>(0, 0); pc[q] = mk<T>(0, 0); }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const int cc = 8 * h + k;
+          const int cc = 2 * k + h;   // halves interleaved: conflict-free for 4- and 8-byte entries
           const T tv = load_c<T>(tile[cc * TB + ((rr + cc) & 15)]);   // T[rr][cc]
 #pragma unroll
           for (int q = 0; q < NR; ++q) pr[q] = cfma(tv, vs[q * mpmax + J * TB + cc], pr[q]);
@@ -469,7 +469,7 @@ k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, c
         if (I != J) {
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            const int ai = 8 * h + k;
+            const int ai = 2 * k + h;
             const T tv = load_c<T>(tile[rr * TB + ((ai + rr) & 15)]);  // T[ai][rr]
 #pragma unroll
             for (int q = 0; q < NR; ++q) pc[q] = cfma(tv, vs[q * mpmax + I * TB + ai], pc[q]);
