@@ -247,7 +247,7 @@ def _givens(a: complex, b: complex):
 
 def fgmres(apply_A: Callable[[np.ndarray], np.ndarray], apply_M: Callable[[np.ndarray], np.ndarray],
            b: np.ndarray, restart: int, rtol: float, max_iters: int,
-           x0: Optional[np.ndarray] = None) -> FGMRESResult:
+           x0: Optional[np.ndarray] = None, reorth: str = "always") -> FGMRESResult:
     """Restarted right-preconditioned flexible GMRES with CGS2 (Sec. 3 outer solver).
 
     Each Arnoldi step: z_j = M v_j, w = A z_j, h = V^H w, w -= V h,
@@ -255,7 +255,12 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray], apply_M: Callable[[np.nd
     update g and the cycle stops at |g_{j+1}| <= rtol ||b||.  Then
     x += Z y with H y = g, and the true residual decides whether to restart.
     ``iters`` counts Arnoldi steps over all cycles.
+
+    ``reorth="selective"`` runs the second Gram-Schmidt pass only when the first
+    one left less than a tenth of ||w|| (Rutishauser's criterion); otherwise h' = 0.
     """
+    if reorth not in ("always", "selective"):
+        raise ValueError(reorth)
     b = np.asarray(b, dtype=np.complex128).ravel()
     bnorm = float(np.linalg.norm(b))
     x = np.zeros_like(b) if x0 is None else np.asarray(x0, dtype=np.complex128).ravel().copy()
@@ -281,11 +286,13 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray], apply_M: Callable[[np.nd
         for j in range(restart):
             Z[j] = apply_M(V[j]).ravel()
             w = apply_A(Z[j])
+            w_norm = float(np.linalg.norm(w))
             h = V[:j + 1].conj() @ w
             w = w - V[:j + 1].T @ h
-            h2 = V[:j + 1].conj() @ w
-            w = w - V[:j + 1].T @ h2
-            h = h + h2
+            if reorth == "always" or np.linalg.norm(w) < 0.1 * w_norm:
+                h2 = V[:j + 1].conj() @ w
+                w = w - V[:j + 1].T @ h2
+                h = h + h2
             hn = float(np.linalg.norm(w))
             H[:j + 1, j] = h
             H[j + 1, j] = hn

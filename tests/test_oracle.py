@@ -224,6 +224,23 @@ def test_fgmres_identity_matches_dense_solve():
     assert abs(res.relres_est - res.relres_true) < 1e-12
 
 
+@pytest.mark.parametrize("reorth", ["always", "selective"])
+def test_fgmres_reorth_modes_match_dense_solve(reorth):
+    """Both Gram-Schmidt variants solve a system whose Krylov vectors become nearly
+    dependent (eigenvalues spread over four decades), where one classical pass alone
+    loses orthogonality; the selective rule must still reach the dense solution."""
+    rng = np.random.default_rng(5)
+    n = 48
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+    A = (Q * np.logspace(0, 4, n)) @ Q.conj().T
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    res = fgmres(lambda v: A @ v, lambda v: v, b, restart=n, rtol=1e-11, max_iters=4 * n, reorth=reorth)
+    assert res.converged and res.iters <= n
+    xs = np.linalg.solve(A, b)
+    assert np.linalg.norm(res.x - xs) / np.linalg.norm(xs) < 1e-9   # cond(A) = 1e4
+    assert np.linalg.norm(b - A @ res.x) / np.linalg.norm(b) <= 1e-11
+
+
 def test_fgmres_restarted_converges():
     rng = np.random.default_rng(1)
     n = 60
