@@ -61,6 +61,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-sample-boxes", type=int, default=2)
     p.add_argument("--arnoldi", default="auto", choices=("auto", "fp64", "ds"))
+    p.add_argument("--reorth", default="selective", choices=("always", "selective"),
+                   help="second Gram-Schmidt pass always (CGS2) or only after a cancellation")
     p.add_argument("--no-autotune", dest="autotune", action="store_false")
     p.add_argument("--symmetric", action="store_true", help="store only the upper tiles of each S_j^{-1}")
     p.add_argument("--overlap", type=int, default=None, help="extra overlap lo in cells (default 8)")
@@ -247,7 +249,7 @@ def run_ours(args, world, rank, local):
         for g0 in range(0, f.shape[0], grp):
             b = s.rhs(f[g0:g0 + grp])
             x, st = s.solve(b, restart=wl.restart, rtol=wl.rtol, max_iters=args.max_iters,
-                            arnoldi=args.arnoldi if precision == args.precision else "fp64")
+                            arnoldi=args.arnoldi if precision == args.precision else "fp64", reorth=args.reorth)
             sts.extend(st)
         tm = s.timers(reset=True)
         s.close()
@@ -299,13 +301,19 @@ def run_ours(args, world, rank, local):
             pass
     traffic = _profile_traffic(wl, args)
     dominant = max(cls_ms, key=lambda c: cls_ms[c])
-    # Arnoldi (CGS2 = 2 dot passes + 2 update passes over the j+1 basis vectors):
-    # FP64 flops (8 per complex multiply-add) and basis bytes (16 per entry and pass)
+    # Arnoldi: each Gram-Schmidt pass is one dot pass and one update pass over the
+    # j+1 basis vectors; the first pass always runs, the second as counted by the
+    # solver.  FP64 flops (8 per complex multiply-add) and bytes (16 per entry and
+    # pass; w is read by the dots, read and written by the update, and the scaling
+    # reads w and writes v_{j+1}).
     arn_flops = arn_bytes = 0
     for it_total in iters:
         for j in _arnoldi_js(it_total, wl.restart):
-            arn_flops += 32 * (j + 1) * n_unk
-            arn_bytes += 4 * (j + 1) * n_unk * 16 + 8 * n_unk * 16
+            arn_flops += 16 * (j + 1) * n_unk
+            arn_bytes += 2 * (j + 1) * n_unk * 16 + 5 * n_unk * 16
+    for s_ in stats:
+        arn_flops += 16 * s_["second_pass_vecs"] * n_unk
+        arn_bytes += 2 * s_["second_pass_vecs"] * n_unk * 16 + 3 * s_["second_passes"] * n_unk * 16
     arn_s = cls_ms["arnoldi"] / 1e3
     ds_mode = args.arnoldi == "ds" or (args.arnoldi == "auto" and args.precision != "c128")
 
@@ -329,6 +337,8 @@ def run_ours(args, world, rank, local):
         "relres_true": ([s["relres_true"] for s in stats] if len(stats) <= 8 else
                         {"max": float(max(s["relres_true"] for s in stats))}),
         "converged": all(s["converged"] == 1 for s in stats),
+        "second_gs_passes": {"steps": int(sum(s["second_passes"] for s in stats)), "of": int(sum(iters)),
+                             "mode": args.reorth},
         "breakdown_ms_per_step": {c: cls_ms[c] / args.steps for c in classes},
         "dominant_kernel_class": dominant,
         "roofline": {"kernel": "k_subst (restrict + forward/back substitution)", "bound": "hbm",
@@ -398,7 +408,7 @@ def run_ours(args, world, rank, local):
         for _ in range(args.e2e_steps):
             _, _, h2d, d2h = solve_host(c_h, f_h, wl.N, wl.npml, wl.omega, wl.nbx, wl.nby, wl.overlap, wl.restart,
                                         wl.rtol, args.max_iters, precision=args.precision, cut_x=wl.cut_x,
-                                        cut_y=wl.cut_y, device=str(dev), arnoldi=args.arnoldi)
+                                        cut_y=wl.cut_y, device=str(dev), arnoldi=args.arnoldi, reorth=args.reorth)
         torch.cuda.synchronize(dev)
         te = max_over_ranks(time.perf_counter() - t0, world)
         out["e2e"] = {"value": world * args.e2e_steps / te, "unit": "solves/s", "h2d_bytes_per_step": h2d,

@@ -183,6 +183,9 @@ typedef struct {
   int32_t graphs;     /* 1: capture each Arnoldi step j (preconditioner, matvec, CGS2,
                          Givens, scaling) once as a CUDA graph per workspace and
                          replay it in later cycles and solves; 0: plain launches   */
+  int32_t reorth;     /* 0: always two Gram-Schmidt passes (CGS2); 1: second pass only
+                         when the first cancelled more than a factor 10 of ||w||
+                         (Rutishauser's criterion, decided on the device)          */
 } hd_gmres_opts;
 
 typedef struct {
@@ -193,6 +196,8 @@ typedef struct {
   double relres_est;    /* |g_{k}| / ||b|| from the Givens recurrence                */
   double relres_true;   /* ||b - A x|| / ||b|| recomputed in FP64                    */
   double t_solve_s;     /* wall time of the solve on the host                        */
+  int32_t second_passes;/* Arnoldi steps that ran the second Gram-Schmidt pass         */
+  int32_t second_pass_vecs; /* basis vectors those second passes went over (sum of j+1) */
 } hd_gmres_stats;
 
 /* Restarted right-preconditioned flexible GMRES (Sec. 3; Z_j = M v_j stored):

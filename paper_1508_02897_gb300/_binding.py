@@ -37,12 +37,13 @@ class hd_decomp(ct.Structure):
 
 class hd_gmres_opts(ct.Structure):
     _fields_ = [("restart", ct.c_int32), ("max_iters", ct.c_int32), ("rtol", ct.c_double), ("use_x0", ct.c_int32),
-                ("arnoldi", ct.c_int32), ("graphs", ct.c_int32)]
+                ("arnoldi", ct.c_int32), ("graphs", ct.c_int32), ("reorth", ct.c_int32)]
 
 
 class hd_gmres_stats(ct.Structure):
     _fields_ = [("iters", ct.c_int32), ("restarts", ct.c_int32), ("converged", ct.c_int32), ("status", ct.c_int32),
-                ("relres_est", ct.c_double), ("relres_true", ct.c_double), ("t_solve_s", ct.c_double)]
+                ("relres_est", ct.c_double), ("relres_true", ct.c_double), ("t_solve_s", ct.c_double),
+                ("second_passes", ct.c_int32), ("second_pass_vecs", ct.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -179,8 +180,9 @@ def hd_apply_precond_noalloc(ctx, r_ptr, z_ptr, nrhs, stream):
 
 
 def hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, restart, max_iters, rtol, krylov_ptr, krylov_bytes, scratch_ptr,
-                   scratch_bytes, stream, use_x0=0, arnoldi=HD_ARNOLDI_FP64, graphs=0, raise_on_not_converged=False):
-    o = hd_gmres_opts(restart, max_iters, rtol, use_x0, arnoldi, graphs)
+                   scratch_bytes, stream, use_x0=0, arnoldi=HD_ARNOLDI_FP64, graphs=0, reorth=0,
+                   raise_on_not_converged=False):
+    o = hd_gmres_opts(restart, max_iters, rtol, use_x0, arnoldi, graphs, reorth)
     st = (hd_gmres_stats * nrhs)()
     allow = () if raise_on_not_converged else (HD_ERR_NOT_CONVERGED,)
     rc = _check("hd_gmres_solve", lib().hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, ct.byref(o), krylov_ptr, krylov_bytes,
@@ -232,13 +234,13 @@ def hd_server_create(hbm_budget_bytes, max_slots, device=0):
 
 def hd_submit(srv, nx, ny, npml, h, omega, c_ptr, f_ptr, nrhs, precision, restart, max_iters, rtol, x_ptr, nbx, nby,
               overlap, cut_x=None, cut_y=None, own_global_pml=1, arnoldi=HD_ARNOLDI_FP64, sigma0_over_omega=20.0,
-              pml_power=2):
+              pml_power=2, reorth=0):
     """Queues a solve; host buffers (c, f, x) must stay alive until hd_poll reports completion."""
     g = hd_grid(nx, ny, npml, h, omega, sigma0_over_omega, pml_power)
     kx, px = _cuts(cut_x)
     ky, py = _cuts(cut_y)
     d = hd_decomp(nbx, nby, overlap, px, py, own_global_pml)
-    o = hd_gmres_opts(restart, max_iters, rtol, 0, arnoldi, 0)
+    o = hd_gmres_opts(restart, max_iters, rtol, 0, arnoldi, 0, reorth)
     t = ct.c_uint64()
     _check("hd_submit", lib().hd_submit(srv, ct.byref(g), ct.byref(d), c_ptr, f_ptr, nrhs, precision, ct.byref(o),
                                         x_ptr, ct.byref(t)))

@@ -314,7 +314,8 @@ int hd_gmres_solve(hd_ctx *c, const void *b, void *x, int32_t nrhs, const hd_gmr
                    void *scratch, size_t scratch_bytes, hd_gmres_stats *stats, void *stream) {
   if (!c || !b || !x || !o || !kws || !scratch || !stats || nrhs < 1) return invalid("hd_gmres_solve: bad argument");
   if (!c->factored) return invalid("hd_gmres_solve: call hd_factor_subdomains first");
-  if (o->restart < 1 || o->max_iters < 0 || !(o->rtol >= 0) || (o->arnoldi != HD_ARNOLDI_FP64 && o->arnoldi != HD_ARNOLDI_DS))
+  if (o->restart < 1 || o->max_iters < 0 || !(o->rtol >= 0) || (o->arnoldi != HD_ARNOLDI_FP64 && o->arnoldi != HD_ARNOLDI_DS) ||
+      (o->reorth != 0 && o->reorth != 1))
     return invalid("hd_gmres_solve: bad options");
   size_t kb, sb;
   hd_query_workspace(c, nrhs, o->restart, nullptr, &kb, &sb);

@@ -97,10 +97,10 @@ struct AxisDev {
 // A captured Arnoldi step (CUDA graph) and the kernels it holds per timer class.
 struct GraphKey {
   const void *kws, *scratch, *factor;
-  int B, R, ds, j, ct, ns;
+  int B, R, mode, j, ct, ns;   // mode: bit 0 double-single Arnoldi, bit 1 selective reorthogonalisation
   bool operator<(const GraphKey &o) const {
-    return std::tie(kws, scratch, factor, B, R, ds, j, ct, ns) <
-           std::tie(o.kws, o.scratch, o.factor, o.B, o.R, o.ds, o.j, o.ct, o.ns);
+    return std::tie(kws, scratch, factor, B, R, mode, j, ct, ns) <
+           std::tie(o.kws, o.scratch, o.factor, o.B, o.R, o.mode, o.j, o.ct, o.ns);
   }
 };
 

@@ -46,10 +46,14 @@ __device__ __forceinline__ double2 warp_sum(double2 v) {
 }
 
 // partial[r][k][blk] = sum over the block's chunk of conj(V_r[k][i]) w_r[i], k < nk.
-__global__ void __launch_bounds__(DT) k_dots(const double2 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
+// With `self`, entry nk is ||w_r||^2; with skip[r] set, the block does nothing.
+__global__ void __launch_bounds__(DT) k_dots(const double2 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk0,
                                              const double2 *__restrict__ w_all, int64_t ldw, int64_t n,
-                                             double2 *__restrict__ partial_all, int G, int64_t ldp) {
+                                             double2 *__restrict__ partial_all, int G, int64_t ldp,
+                                             const int *__restrict__ skip, int self) {
   extern __shared__ double2 red[];  // [DT/32][nk]
+  if (skip && skip[blockIdx.y]) return;
+  const int nk = nk0 + self;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double2 *w = w_all + (int64_t)blockIdx.y * ldw;
   const double2 *Vr = V + (int64_t)blockIdx.y * ldvr;
@@ -67,7 +71,7 @@ __global__ void __launch_bounds__(DT) k_dots(const double2 *__restrict__ V, int6
 #pragma unroll
     for (int e = 0; e < DE; ++e) {
       int64_t i = base + (int64_t)DT * e;
-      if (i < n) acc = cfma_conj(vk[i], wv[e], acc);
+      if (i < n) acc = cfma_conj(k < nk0 ? vk[i] : wv[e], wv[e], acc);
     }
     acc = warp_sum(acc);
     if (lane == 0) red[warp * nk + k] = acc;
@@ -80,11 +84,17 @@ __global__ void __launch_bounds__(DT) k_dots(const double2 *__restrict__ V, int6
   }
 }
 
-// out[r*ldo + k] = sum_b partial[r][k][b] in a fixed order; grid (nk, nrhs).
+// out[r*ldo + k] = sum_b partial[r][k][b] in a fixed order; grid (nk, nrhs).  For a
+// skipped right-hand side the output is zeroed (skip_mode 1) or left as it is (2).
 __global__ void __launch_bounds__(256) k_reduce(const double2 *__restrict__ partial, int G, int64_t ldp,
-                                                double2 *__restrict__ out, int ldo) {
+                                                double2 *__restrict__ out, int ldo, const int *__restrict__ skip = nullptr,
+                                                int skip_mode = 0) {
   __shared__ double2 sm[256];
   const int k = blockIdx.x, tid = threadIdx.x;
+  if (skip && skip[blockIdx.y]) {
+    if (skip_mode == 1 && tid == 0) out[(int64_t)blockIdx.y * ldo + k] = make_double2(0.0, 0.0);
+    return;
+  }
   const double2 *p = partial + (int64_t)blockIdx.y * ldp + (int64_t)k * G;
   double2 acc = make_double2(0.0, 0.0);
   for (int b = tid; b < G; b += 256) acc = cadd(acc, p[b]);
@@ -103,10 +113,12 @@ template <bool NORM>
 __global__ void __launch_bounds__(DT) k_update(const double2 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
                                                const int *__restrict__ nk_per, const double2 *__restrict__ coef_all,
                                                int ldc, double sgn, const double2 *base_all, double2 *y_all, int64_t ldy,
-                                               int64_t n, double2 *__restrict__ normpart_all, int64_t ldp) {
+                                               int64_t n, double2 *__restrict__ normpart_all, int64_t ldp,
+                                               const int *__restrict__ skip) {
   extern __shared__ double2 cs[];  // [nk]
   __shared__ double nsm[DT / 32];
   const int tid = threadIdx.x, r = blockIdx.y;
+  if (skip && skip[r]) return;
   const int nkr = nk_per ? nk_per[r] : nk;
   const double2 *coef = coef_all + (int64_t)r * ldc;
   const double2 *Vr = V + (int64_t)r * ldvr;
@@ -205,10 +217,14 @@ __device__ __forceinline__ void ds_add(float &sh, float &sl, float bh, float bl)
 }
 
 // partial[r][k][blk] = sum over the block's DFC elements of conj(V_r[k][i]) w_r[i].
-__global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
+// With `self`, entry nk is ||w_r||^2; with skip[r] set, the block does nothing.
+__global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk0,
                                                  const double2 *__restrict__ w_all, int64_t ldw, int64_t n,
-                                                 double2 *__restrict__ partial_all, int G, int64_t ldp) {
+                                                 double2 *__restrict__ partial_all, int G, int64_t ldp,
+                                                 const int *__restrict__ skip, int self) {
   extern __shared__ float4 wsm[];  // [DFC]
+  if (skip && skip[blockIdx.y]) return;
+  const int nk = nk0 + self;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t base = (int64_t)blockIdx.x * DFC;
   const int cnt = (int)min((int64_t)DFC, n - base);
@@ -233,7 +249,7 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, i
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         int i = i0 + u * 32 + lane;
-        vv[u] = i < cnt ? vk[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        vv[u] = i < cnt ? (k < nk0 ? vk[i] : wsm[i]) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
@@ -265,10 +281,12 @@ template <bool NORM>
 __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
                                                   const double2 *__restrict__ coef_all, int ldc, const double2 *base_all,
                                                   double2 *y_all, int64_t ldy, int64_t n,
-                                                  double2 *__restrict__ normpart_all, int64_t ldp) {
+                                                  double2 *__restrict__ normpart_all, int64_t ldp,
+                                                  const int *__restrict__ skip) {
   extern __shared__ float4 csm[];  // [nk]
   __shared__ double nsm[DT / 32];
   const int tid = threadIdx.x, r = blockIdx.y;
+  if (skip && skip[r]) return;
   const double2 *coef = coef_all + (int64_t)r * ldc;
   const float4 *Vr = V + (int64_t)r * ldvr;
   const double2 *base = base_all + (int64_t)r * ldy;
@@ -364,6 +382,17 @@ struct GmresDev {
 };
 
 __device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, a.y); }
+
+// Selective reorthogonalisation (Rutishauser): the second Gram-Schmidt pass runs
+// only if the first one cancelled more than a factor 10 of ||w||, i.e.
+// ||w - V h|| < ||w|| / 10; h1[nk] holds ||w||^2 and red[4 r] ||w - V h||^2.
+__global__ void k_reorth_decide(GmresDev d, int nk, int *skip) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= d.nrhs) return;
+  const double w2 = d.h1[(int64_t)r * d.ldh + nk].x, w1 = d.red[4 * r].x;
+  skip[r] = (w1 >= 0.01 * w2) ? 1 : 0;
+  d.stat[4 * r + 3] = (w1 >= 0.01 * w2) ? 0.0 : 1.0;   // second pass taken in this step
+}
 
 __global__ void k_cycle_init(GmresDev d) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -479,7 +508,7 @@ static KrylovLayout krylov_layout(int64_t n, int restart, int nrhs) {
   L.off_g = o; o += al(c16 * (R + 1) * B);
   L.off_y = o; o += al(c16 * R * B);
   L.off_stat = o; o += al(sizeof(double) * 4 * B);
-  L.off_live = o; o += al(sizeof(int) * 2 * B);   // live [B] followed by kcnt [B]
+  L.off_live = o; o += al(sizeof(int) * 3 * B);   // live [B], kcnt [B], skip [B]
   L.total = o;
   return L;
 }
@@ -509,42 +538,51 @@ struct Krylov {
   int64_t ldvr() const { return L.n * (L.restart + 1); }
   int64_t ldp() const { return (int64_t)L.Gmax * (L.restart + 1); }
 
-  // out[r*ldo + k] = V_r[k]^H x_r, k < nk (V given with its per-RHS stride)
-  cudaError_t dots(const double2 *Vb, int64_t vr, int nk, const double2 *x, double2 *out, int ldo) {
+  // out[r*ldo + k] = V_r[k]^H x_r, k < nk (V given with its per-RHS stride); with self,
+  // out[r*ldo + nk] = ||x_r||^2; skipped right-hand sides get zeros.
+  cudaError_t dots(const double2 *Vb, int64_t vr, int nk, const double2 *x, double2 *out, int ldo,
+                   const int *skip = nullptr, int self = 0) {
     tic(ctx, T_ARNOLDI, st);
-    k_dots<<<dim3(L.G, B), DT, sizeof(double2) * (DT / 32) * nk, st>>>(Vb, L.n, vr, nk, x, L.n, L.n, part(), L.G, ldp());
-    k_reduce<<<dim3(nk, B), 256, 0, st>>>(part(), L.G, ldp(), out, ldo);
+    k_dots<<<dim3(L.G, B), DT, sizeof(double2) * (DT / 32) * (nk + self), st>>>(Vb, L.n, vr, nk, x, L.n, L.n, part(),
+                                                                               L.G, ldp(), skip, self);
+    k_reduce<<<dim3(nk + self, B), 256, 0, st>>>(part(), L.G, ldp(), out, ldo, skip, 1);
     toc(ctx, T_ARNOLDI, st, 2);
     return cudaGetLastError();
   }
+  // y_r = base_r + sgn V_r c_r; norm_out[4 r] = ||y_r||^2 (left unchanged for skipped ones).
   cudaError_t update(const double2 *Vb, int64_t vr, int nk, const int *nk_per, const double2 *coef, int ldc,
-                     double sgn, const double2 *base, double2 *y, double2 *norm_out) {
+                     double sgn, const double2 *base, double2 *y, double2 *norm_out, const int *skip = nullptr) {
     tic(ctx, T_ARNOLDI, st);
     size_t sm = sizeof(double2) * std::max(nk, 1);
     if (norm_out) {
-      k_update<true><<<dim3(L.G, B), DT, sm, st>>>(Vb, L.n, vr, nk, nk_per, coef, ldc, sgn, base, y, L.n, L.n, part(), ldp());
-      k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4);
+      k_update<true><<<dim3(L.G, B), DT, sm, st>>>(Vb, L.n, vr, nk, nk_per, coef, ldc, sgn, base, y, L.n, L.n, part(),
+                                                   ldp(), skip);
+      k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4, skip, 2);
     } else {
-      k_update<false><<<dim3(L.G, B), DT, sm, st>>>(Vb, L.n, vr, nk, nk_per, coef, ldc, sgn, base, y, L.n, L.n, nullptr, 0);
+      k_update<false><<<dim3(L.G, B), DT, sm, st>>>(Vb, L.n, vr, nk, nk_per, coef, ldc, sgn, base, y, L.n, L.n,
+                                                    nullptr, 0, skip);
     }
     toc(ctx, T_ARNOLDI, st, norm_out ? 2 : 1);
     return cudaGetLastError();
   }
-  cudaError_t dots_df(int nk, const double2 *x, double2 *out, int ldo) {
+  cudaError_t dots_df(int nk, const double2 *x, double2 *out, int ldo, const int *skip = nullptr, int self = 0) {
     tic(ctx, T_ARNOLDI, st);
-    k_dots_df<<<dim3(L.Gdf, B), 256, sizeof(float4) * DFC, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp());
-    k_reduce<<<dim3(nk, B), 256, 0, st>>>(part(), L.Gdf, ldp(), out, ldo);
+    k_dots_df<<<dim3(L.Gdf, B), 256, sizeof(float4) * DFC, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf,
+                                                                ldp(), skip, self);
+    k_reduce<<<dim3(nk + self, B), 256, 0, st>>>(part(), L.Gdf, ldp(), out, ldo, skip, 1);
     toc(ctx, T_ARNOLDI, st, 2);
     return cudaGetLastError();
   }
-  cudaError_t update_df(int nk, const double2 *coef, int ldc, double2 *wv, double2 *norm_out) {
+  cudaError_t update_df(int nk, const double2 *coef, int ldc, double2 *wv, double2 *norm_out, const int *skip = nullptr) {
     tic(ctx, T_ARNOLDI, st);
     size_t sm = sizeof(float4) * nk;
     if (norm_out) {
-      k_update_df<true><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, wv, wv, L.n, L.n, part(), ldp());
-      k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4);
+      k_update_df<true><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, wv, wv, L.n, L.n, part(), ldp(),
+                                                      skip);
+      k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4, skip, 2);
     } else {
-      k_update_df<false><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, wv, wv, L.n, L.n, nullptr, 0);
+      k_update_df<false><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, wv, wv, L.n, L.n, nullptr, 0,
+                                                       skip);
     }
     toc(ctx, T_ARNOLDI, st, norm_out ? 2 : 1);
     return cudaGetLastError();
@@ -589,6 +627,8 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
   d.stat = K.at<double>(K.L.off_stat);
   d.live = K.at<int>(K.L.off_live);
   d.kcnt = d.live + B;
+  int *skip = d.live + 2 * B;
+  const bool sel = o->reorth == 1;
   d.ldh = R + 1; d.restart = R; d.nrhs = B;
   const bool dsm = o->arnoldi == HD_ARNOLDI_DS;
   if (dsm) KCHK(cudaFuncSetAttribute(k_dots_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float4) * DFC)));
@@ -619,7 +659,7 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
   int rc = read_red();
   if (rc) return rc;
   std::vector<double> bnorm(B), rel_est(B, 1.0), rel_true(B, 1.0);
-  std::vector<int> iters(B, 0), done(B, 0), conv(B, 0), status(B, HD_OK);
+  std::vector<int> iters(B, 0), done(B, 0), conv(B, 0), status(B, HD_OK), passes2(B, 0), vecs2(B, 0);
   for (int r = 0; r < B; ++r) bnorm[r] = std::sqrt(h_red[4 * r].x);
   if (!o->use_x0) KCHK(cudaMemsetAsync(x, 0, sizeof(double2) * n * B, st));
   int cycles = 0;
@@ -666,17 +706,24 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
       tic(ctx, T_MATVEC, st);
       KCHK(launch_matvec(ctx, zj, zs, K.w(), n, B, st));
       toc(ctx, T_MATVEC, st, 1);
+      // CGS2: h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2; with selective
+      // reorthogonalisation the second pass is skipped (h2 = 0) unless the first
+      // cancelled more than a factor 10 of ||w||.
+      const int self = sel ? 1 : 0;
       if (dsm) {
-        KCHK(K.dots_df(j + 1, K.w(), d.h1, R + 1));
-        KCHK(K.update_df(j + 1, d.h1, R + 1, K.w(), nullptr));
-        KCHK(K.dots_df(j + 1, K.w(), d.h2, R + 1));
-        KCHK(K.update_df(j + 1, d.h2, R + 1, K.w(), d.red));
+        KCHK(K.dots_df(j + 1, K.w(), d.h1, R + 1, nullptr, self));
+        KCHK(K.update_df(j + 1, d.h1, R + 1, K.w(), sel ? d.red : nullptr));
+        if (sel) k_reorth_decide<<<nb, tb, 0, st>>>(d, j + 1, skip);
+        KCHK(K.dots_df(j + 1, K.w(), d.h2, R + 1, sel ? skip : nullptr));
+        KCHK(K.update_df(j + 1, d.h2, R + 1, K.w(), d.red, sel ? skip : nullptr));
       } else {
-        KCHK(K.dots(K.V(), K.ldvr(), j + 1, K.w(), d.h1, R + 1));
-        KCHK(K.update(K.V(), K.ldvr(), j + 1, nullptr, d.h1, R + 1, -1.0, K.w(), K.w(), nullptr));
-        KCHK(K.dots(K.V(), K.ldvr(), j + 1, K.w(), d.h2, R + 1));
-        KCHK(K.update(K.V(), K.ldvr(), j + 1, nullptr, d.h2, R + 1, -1.0, K.w(), K.w(), d.red));
+        KCHK(K.dots(K.V(), K.ldvr(), j + 1, K.w(), d.h1, R + 1, nullptr, self));
+        KCHK(K.update(K.V(), K.ldvr(), j + 1, nullptr, d.h1, R + 1, -1.0, K.w(), K.w(), sel ? d.red : nullptr));
+        if (sel) k_reorth_decide<<<nb, tb, 0, st>>>(d, j + 1, skip);
+        KCHK(K.dots(K.V(), K.ldvr(), j + 1, K.w(), d.h2, R + 1, sel ? skip : nullptr));
+        KCHK(K.update(K.V(), K.ldvr(), j + 1, nullptr, d.h2, R + 1, -1.0, K.w(), K.w(), d.red, sel ? skip : nullptr));
       }
+      if (sel) ctx->t_launch[T_ARNOLDI] += 1;
       tic(ctx, T_ARNOLDI, st);
       k_arnoldi_step<<<nb, tb, 0, st>>>(d, j);
       if (dsm) k_scale_df<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.Vdf() + (int64_t)(j + 1) * n, K.ldvr(), K.vin(), n);
@@ -688,7 +735,7 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
     for (int j = 0; j < R; ++j) {
       if (o->graphs) {
         // each step j is captured once per workspace/launch shape and then replayed
-        const GraphKey key{kws, scratch, ctx->factor, B, R, dsm ? 1 : 0, j, ctx->tune_ct, ctx->tune_ns};
+        const GraphKey key{kws, scratch, ctx->factor, B, R, (dsm ? 1 : 0) | (sel ? 2 : 0), j, ctx->tune_ct, ctx->tune_ns};
         auto it = ctx->graphs.find(key);
         if (it == ctx->graphs.end()) {
           const bool prof = ctx->profiling;
@@ -727,6 +774,7 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
         ++iters[r];
         h_kcnt[r] = j + 1;
         const double *sr = h_stat + 4 * r;
+        if (!sel || sr[3] != 0.0) { ++passes2[r]; vecs2[r] += j + 1; }
         bool stop = false;
         if (sr[2] != 0.0) { status[r] = HD_ERR_NUMERIC; done[r] = 1; stop = true; }
         rel_est[r] = bnorm[r] > 0 ? sr[0] / bnorm[r] : 0.0;
@@ -755,6 +803,8 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
     sr.relres_est = rel_est[r];
     sr.relres_true = rel_true[r];
     sr.t_solve_s = ts;
+    sr.second_passes = passes2[r];
+    sr.second_pass_vecs = vecs2[r];
     sr.status = status[r] != HD_OK ? status[r] : (conv[r] ? HD_OK : HD_ERR_NOT_CONVERGED);
     if (sr.status == HD_ERR_NUMERIC) worst = HD_ERR_NUMERIC;
     else if (sr.status && !worst) worst = sr.status;

@@ -102,9 +102,11 @@ class HelmholtzDDM:
         return self._krylov[key]
 
     def solve(self, b, restart: int = 50, rtol: float = 1e-8, max_iters: int = 1000, x0=None, out=None,
-              arnoldi: str = "auto", graphs: bool = False):
+              arnoldi: str = "auto", graphs: bool = False, reorth: str = "selective"):
         """FGMRES solve of A x = b.  ``arnoldi``: "fp64", "ds" (double-single
-        Gram-Schmidt on the FP32 pipes) or "auto" (ds with FP32 factors, fp64 with c128)."""
+        Gram-Schmidt on the FP32 pipes) or "auto" (ds with FP32 factors, fp64 with c128).
+        ``reorth``: "always" (CGS2) or "selective" (second pass only after a cancellation
+        of more than a factor 10)."""
         b, nrhs = self._vec(b)
         if out is not None:
             x = out
@@ -116,7 +118,7 @@ class HelmholtzDDM:
         rc, stats = B.hd_gmres_solve(self.ctx, b.data_ptr(), x.data_ptr(), nrhs, restart, max_iters, rtol,
                                      kws.data_ptr(), kws.numel(), self.scratch.data_ptr(), self.scratch_bytes,
                                      self._st(), use_x0=int(x0 is not None), arnoldi=self._arnoldi(arnoldi),
-                                     graphs=int(graphs))
+                                     graphs=int(graphs), reorth={"always": 0, "selective": 1}[reorth])
         return x, stats
 
     def _arnoldi(self, mode: str) -> int:
@@ -144,7 +146,7 @@ class HelmholtzDDM:
 
 def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: int, overlap: int,
                restart: int, rtol: float, max_iters: int = 5000, precision: str = "c64", cut_x=None, cut_y=None,
-               device: str = "cuda", arnoldi: str = "auto", symmetric: bool = False):
+               device: str = "cuda", arnoldi: str = "auto", symmetric: bool = False, reorth: str = "selective"):
     """End-to-end solve from host arrays: velocity c [n][n] (float64) and source
     samples f [nrhs][n][n] (complex128), preferably in pinned memory.  Copies in,
     sets up the medium, factorises, forms b = J h^2 f, runs FGMRES and copies the
@@ -155,7 +157,7 @@ def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: i
     s = HelmholtzDDM(N, npml, omega, c_d, nbx, nby, overlap, precision=precision, cut_x=cut_x, cut_y=cut_y,
                      device=device, symmetric=symmetric)
     b = s.rhs(f_d)
-    x, stats = s.solve(b, restart=restart, rtol=rtol, max_iters=max_iters, arnoldi=arnoldi)
+    x, stats = s.solve(b, restart=restart, rtol=rtol, max_iters=max_iters, arnoldi=arnoldi, reorth=reorth)
     x_h = x.to("cpu")
     s.close()
     h2d = c_d.numel() * c_d.element_size() + f_d.numel() * f_d.element_size()
@@ -171,7 +173,7 @@ class Server:
         self._keep = {}
 
     def submit(self, c, f, N, npml, omega, nbx, nby, overlap, restart, rtol, max_iters=5000, precision="c64",
-               cut_x=None, cut_y=None, arnoldi="auto", symmetric=False):
+               cut_x=None, cut_y=None, arnoldi="auto", symmetric=False, reorth="selective"):
         """c: float64 [n][n], f: complex128 [nrhs][n][n] host arrays.  Returns a ticket."""
         c = np.ascontiguousarray(c, dtype=np.float64)
         f = np.ascontiguousarray(f, dtype=np.complex128)
@@ -183,7 +185,8 @@ class Server:
         t = B.hd_submit(self.srv, N, N, npml, 1.0 / N, omega, c.ctypes.data, f.ctypes.data, f.shape[0],
                         prec | (B.HD_SYMMETRIC if symmetric else 0),
                         restart, max_iters, rtol, x.ctypes.data, nbx, nby, overlap, cut_x, cut_y,
-                        arnoldi={"fp64": B.HD_ARNOLDI_FP64, "ds": B.HD_ARNOLDI_DS}[mode])
+                        arnoldi={"fp64": B.HD_ARNOLDI_FP64, "ds": B.HD_ARNOLDI_DS}[mode],
+                        reorth={"always": 0, "selective": 1}[reorth])
         self._keep[t] = (c, f, x)
         return t
 

@@ -96,29 +96,32 @@ def test_precond_literal_ownership():
 
 @pytest.mark.parametrize("name", ["tiny", "ragged"])
 @pytest.mark.parametrize("arnoldi", ["fp64", "ds"])
-def test_gmres_fixed_steps_c128(name, arnoldi):
+@pytest.mark.parametrize("reorth", ["always", "selective"])
+def test_gmres_fixed_steps_c128(name, arnoldi, reorth):
     """Same FGMRES variant on both sides: the iterate after k steps agrees
-    (FP64 Gram-Schmidt, and the double-single one whose basis carries ~48 bits)."""
+    (FP64 Gram-Schmidt, and the double-single one whose basis carries ~48 bits;
+    two passes always, or the second only after a cancellation)."""
     case, c, g, A, P = oracle(name)
     s = gpu(name, "c128")
     f = W.gaussian_source(case["N"], case["npml"], 0.45, 0.55, 2.0 / case["N"])
     b = rhs_from_source(g, f)
     k = 4
-    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=3, rtol=1e-15, max_iters=k)
-    x, st = s.solve(torch.from_numpy(b), restart=3, rtol=1e-15, max_iters=k, arnoldi=arnoldi)
+    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=3, rtol=1e-15, max_iters=k, reorth=reorth)
+    x, st = s.solve(torch.from_numpy(b), restart=3, rtol=1e-15, max_iters=k, arnoldi=arnoldi, reorth=reorth)
     assert st[0]["iters"] == ref.iters == k
     assert rel(x.cpu().numpy(), ref.x.reshape(g.n, g.n)) < 1e-9
 
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("arnoldi", ["fp64", "ds"])
-def test_gmres_converged_c128(name, arnoldi):
+@pytest.mark.parametrize("reorth", ["always", "selective"])
+def test_gmres_converged_c128(name, arnoldi, reorth):
     case, c, g, A, P = oracle(name)
     s = gpu(name, "c128")
     f = W.gaussian_source(case["N"], case["npml"], 0.5, 0.5, 2.0 / case["N"])
     b = rhs_from_source(g, f)
-    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=50, rtol=1e-8, max_iters=300)
-    x, st = s.solve(torch.from_numpy(b), restart=50, rtol=1e-8, max_iters=300, arnoldi=arnoldi)
+    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=50, rtol=1e-8, max_iters=300, reorth=reorth)
+    x, st = s.solve(torch.from_numpy(b), restart=50, rtol=1e-8, max_iters=300, arnoldi=arnoldi, reorth=reorth)
     assert st[0]["converged"] == 1 and abs(st[0]["iters"] - ref.iters) <= 1
     xn = x.cpu().numpy().ravel()
     assert np.linalg.norm(b.ravel() - A @ xn) / np.linalg.norm(b) <= 1e-8
@@ -215,16 +218,16 @@ def test_autotune_keeps_results():
     assert np.array_equal(z0, z1)
 
 
-@pytest.mark.parametrize("precision", ["c128", "c64"])
-def test_gmres_graph_capture_matches_launches(precision):
+@pytest.mark.parametrize("precision,reorth", [("c128", "always"), ("c64", "selective"), ("c128", "selective")])
+def test_gmres_graph_capture_matches_launches(precision, reorth):
     """Arnoldi steps captured once as CUDA graphs and replayed (second solve on the
     same workspace) give bitwise the solution of plain launches."""
     case, c, g, A, P = oracle("ragged")
     s = gpu("ragged", precision)
     b = rhs_from_source(g, W.gaussian_source(case["N"], case["npml"], 0.35, 0.6, 2.0 / case["N"]))
-    x0, st0 = s.solve(torch.from_numpy(b), restart=10, rtol=1e-9, max_iters=200)
-    x1, st1 = s.solve(torch.from_numpy(b), restart=10, rtol=1e-9, max_iters=200, graphs=True)
-    x2, st2 = s.solve(torch.from_numpy(b), restart=10, rtol=1e-9, max_iters=200, graphs=True)
+    x0, st0 = s.solve(torch.from_numpy(b), restart=10, rtol=1e-9, max_iters=200, reorth=reorth)
+    x1, st1 = s.solve(torch.from_numpy(b), restart=10, rtol=1e-9, max_iters=200, graphs=True, reorth=reorth)
+    x2, st2 = s.solve(torch.from_numpy(b), restart=10, rtol=1e-9, max_iters=200, graphs=True, reorth=reorth)
     assert st0[0]["iters"] == st1[0]["iters"] == st2[0]["iters"] and st2[0]["converged"] == 1
     assert np.array_equal(x0.cpu().numpy(), x1.cpu().numpy())
     assert np.array_equal(x0.cpu().numpy(), x2.cpu().numpy())
