@@ -64,7 +64,10 @@ def parse():
     p.add_argument("--reorth", default="selective", choices=("always", "selective"),
                    help="second Gram-Schmidt pass always (CGS2) or only after a cancellation")
     p.add_argument("--no-autotune", dest="autotune", action="store_false")
-    p.add_argument("--symmetric", action="store_true", help="store only the upper tiles of each S_j^{-1}")
+    p.add_argument("--storage", default="sym", choices=("sym", "full"),
+                   help="S_j^{-1} storage: upper 16x16 tiles only (sym, default) or full blocks")
+    p.add_argument("--symmetric", dest="storage", action="store_const", const="sym", help="same as --storage sym")
+    p.add_argument("--full-blocks", dest="storage", action="store_const", const="full", help="same as --storage full")
     p.add_argument("--overlap", type=int, default=None, help="extra overlap lo in cells (default 8)")
     p.add_argument("--probe-peaks", action="store_true", help="also measure FP64/FP32 FMA and copy rates")
     p.add_argument("--npml", type=int, default=None, help="PML cells per side (default 16)")
@@ -194,19 +197,27 @@ def _rhs_per_cta(k):
     return 8 if k >= 8 else (4 if k >= 4 else (2 if k >= 2 else 1))
 
 
-def subst_bytes(wl, cs: int, nrhs: int = 1, fs: int = None) -> int:
-    """Algorithmic HBM bytes of one k_subst launch (one preconditioner application
-    to nrhs vectors): every stored S_j^{-1} read once forward and once backward (the
-    last row once) per group of right-hand sides sharing a CTA, the owned residual
-    read once (FP64 complex), the staging vector written forward, read and
-    rewritten backward."""
+def block_entries(m: int, sym: bool) -> int:
+    """Stored entries of one S_j^{-1}: m^2, or the upper 16x16 tiles only."""
+    if not sym:
+        return m * m
+    mt = -(-m // 16)
+    return mt * (mt + 1) // 2 * 256
+
+
+def subst_bytes(wl, cs: int, nrhs: int = 1, fs: int = None, sym: bool = False) -> int:
+    """Algorithmic HBM bytes of one substitution launch (one preconditioner
+    application to nrhs vectors): every stored S_j^{-1} read once forward and once
+    backward (the last row once) per group of right-hand sides sharing a CTA, the
+    owned residual read once (FP64 complex), the staging vector written forward,
+    read and rewritten backward."""
     groups = -(-nrhs // _rhs_per_cta(nrhs))
     tot = 16 * wl.n * wl.n * nrhs
     for iy in range(wl.nby):
         for ix in range(wl.nbx):
             m = _extent(wl.cut_x, ix, wl)
             rows = _extent(wl.cut_y, iy, wl)
-            tot += (2 * rows - 1) * m * m * (fs or cs) * groups + 3 * rows * m * cs * nrhs
+            tot += (2 * rows - 1) * block_entries(m, sym) * (fs or cs) * groups + 3 * rows * m * cs * nrhs
     return tot
 
 
@@ -240,7 +251,8 @@ def run_ours(args, world, rank, local):
         f = f_d if f is None else f
         grp = group if grp is None else grp
         s = HelmholtzDDM(wl.N, wl.npml, wl.omega, c_d, wl.nbx, wl.nby, wl.overlap, precision=precision,
-                         cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev), symmetric=args.symmetric)
+                         cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev),
+                         symmetric=args.storage == "sym")
         s.set_profiling(profile)
         s.factor()
         if args.autotune:
@@ -288,7 +300,8 @@ def run_ours(args, world, rank, local):
     launches = int(sum(cls_n.values()))
     cs = 16 if args.precision == "c128" else 8                       # staging (compute) entry
     fs = {"c128": 16, "c64": 8, "c64h": 4}[args.precision]          # stored factor entry
-    sb = subst_bytes(wl, cs, group, fs)
+    sym = args.storage == "sym"
+    sb = subst_bytes(wl, cs, group, fs, sym)
     sub_avg_ms = cls_ms["subst"] / max(cls_n["subst"], 1)
     achieved = sb / (sub_avg_ms / 1e3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -327,7 +340,8 @@ def run_ours(args, world, rank, local):
         "config": {"workload": describe(wl, args.precision), "N": wl.N, "npml": wl.npml, "boxes": [wl.nbx, wl.nby],
                    "overlap": wl.overlap, "restart": wl.restart, "rtol": wl.rtol, "precision": args.precision,
                    "omega": wl.omega, "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)" % (
-                       _factor_gb(wl, fs), 2 * (wl.restart + 1) * n_unk * 16 / 1e9),
+                       _factor_gb(wl, fs, sym), 2 * (wl.restart + 1) * n_unk * 16 / 1e9),
+                   "factor_storage": "upper 16x16 tiles (symmetric)" if sym else "full blocks",
                    "parallelism": f"replicas x{world} (one independent solve per GPU)"},
         "unknown_iters_per_s": unk_iters,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -341,7 +355,8 @@ def run_ours(args, world, rank, local):
                              "mode": args.reorth},
         "breakdown_ms_per_step": {c: cls_ms[c] / args.steps for c in classes},
         "dominant_kernel_class": dominant,
-        "roofline": {"kernel": "k_subst (restrict + forward/back substitution)", "bound": "hbm",
+        "roofline": {"kernel": ("k_subst_sym" if sym else "k_subst") + " (restrict + forward/back substitution)",
+                     "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_src, "bytes_per_launch": sb,
                      "traffic": traffic, "launches": cls_n["subst"], "avg_launch_ms": sub_avg_ms},
@@ -408,7 +423,8 @@ def run_ours(args, world, rank, local):
         for _ in range(args.e2e_steps):
             _, _, h2d, d2h = solve_host(c_h, f_h, wl.N, wl.npml, wl.omega, wl.nbx, wl.nby, wl.overlap, wl.restart,
                                         wl.rtol, args.max_iters, precision=args.precision, cut_x=wl.cut_x,
-                                        cut_y=wl.cut_y, device=str(dev), arnoldi=args.arnoldi, reorth=args.reorth)
+                                        cut_y=wl.cut_y, device=str(dev), arnoldi=args.arnoldi, reorth=args.reorth,
+                                        symmetric=args.storage == "sym")
         torch.cuda.synchronize(dev)
         te = max_over_ranks(time.perf_counter() - t0, world)
         out["e2e"] = {"value": world * args.e2e_steps / te, "unit": "solves/s", "h2d_bytes_per_step": h2d,
@@ -438,32 +454,35 @@ def _arnoldi_js(iters_total, restart):
     return js
 
 
-def _factor_gb(wl, cs):
+def _factor_gb(wl, cs, sym=False):
     tot = 0
     for iy in range(wl.nby):
         for ix in range(wl.nbx):
-            tot += _extent(wl.cut_y, iy, wl) * _extent(wl.cut_x, ix, wl) ** 2
+            tot += _extent(wl.cut_y, iy, wl) * block_entries(_extent(wl.cut_x, ix, wl), sym)
     return tot * cs / 1e9
 
 
 def _profile_traffic(wl, args):
     """DRAM bytes per k_subst launch from the committed ncu summary, scaled to
     this workload, when it matches the current kernel (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_subst_traffic.json")
+    name = "k_subst_sym_traffic.json" if args.storage == "sym" else "k_subst_traffic.json"
+    path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     try:
         d = json.load(open(path))
-        if d.get("precision") != args.precision or d.get("kernel_rev") != KERNEL_REV:
+        sym = args.storage == "sym"
+        if (d.get("precision") != args.precision or d.get("kernel_rev") != KERNEL_REV[sym]
+                or d.get("storage", "full") != args.storage):
             return None
         cs = 16 if args.precision == "c128" else 8
         fs = {"c128": 16, "c64": 8, "c64h": 4}[args.precision]
-        return d["dram_bytes_per_launch"] * subst_bytes(wl, cs, 1, fs) / d["algorithmic_bytes_per_launch"]
+        return d["dram_bytes_per_launch"] * subst_bytes(wl, cs, 1, fs, sym) / d["algorithmic_bytes_per_launch"]
     except Exception:
         return None
 
 
-KERNEL_REV = "subst-v3"
+KERNEL_REV = {False: "subst-v3", True: "subst-sym-v2"}   # kernel revisions the traffic summaries describe
 
 
 # ----------------------------------------------------------------------------- serving
@@ -498,7 +517,8 @@ def run_serving(args, world, rank, local):
         if t_arr > now:
             time.sleep(t_arr - now)
         tickets.append((srv.submit(wl.c, wl.f, wl.N, wl.npml, wl.omega, wl.nbx, wl.nby, wl.overlap, wl.restart,
-                                   wl.rtol, args.max_iters), wl))
+                                   wl.rtol, args.max_iters, symmetric=args.storage == "sym",
+                                   reorth=args.reorth), wl))
     lat, solves, ok, unk_it = [], 0, 0, 0.0
     for t, wl in tickets:
         x, stats, info = srv.poll(t)

@@ -299,20 +299,22 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
 // (the rotation keeps row- and column-wise reads free of bank conflicts).
 // This streams about (mt+1)/(2 mt) of the bytes of the full blocks.  A tile
 // (I, J) serves twice: y_I += T v_J and, off the diagonal, y_J += T^T v_I.
-// Tile-column J belongs to consumer warp min(J, mt-1-J) mod NW (pairing long
-// and short columns); in a warp, lane (rr, h) covers row / column rr of the
-// tile and the terms of parity h.  Column-wise sums stay in registers until
-// the column's diagonal tile; row-wise sums go to a per-warp partial vector in
-// shared memory; the step ends with y[a] = sum over warps of the partials.
+// A ring stage holds NW * TPW consecutive tiles and every consumer warp takes
+// TPW of them (tile du of a stage belongs to warp du % NW), so all warps work
+// on every stage.  In a warp, lane (rr, h) covers row / column rr of the tile
+// and the terms of parity h; after one shuffle the h = 0 lanes add the row-wise
+// sums and the h = 1 lanes the column-wise sums into the warp's own partial
+// vector in shared memory, and the step ends with y[a] = sum over warps of the
+// partials (a fixed order: results do not depend on timing).
 constexpr int TB = 16;
 
-template <typename S> __host__ __device__ constexpr int tiles_per_stage() {
-  return sizeof(S) == 16 ? 2 : (sizeof(S) == 8 ? 4 : 8);   // 8 KB stages
+template <typename S> __host__ __device__ constexpr int sym_tiles_per_warp() {
+  return sizeof(S) == 16 ? 1 : (sizeof(S) == 8 ? 1 : 2);
 }
 
 template <typename T, typename S>
 __host__ __device__ inline size_t subst_sym_smem(int ns, int mp, int nw, int nr, int nt) {
-  size_t o = (size_t)ns * tiles_per_stage<S>() * TB * TB * sizeof(S);
+  size_t o = (size_t)ns * nw * sym_tiles_per_warp<S>() * TB * TB * sizeof(S);
   o += (size_t)nr * mp * sizeof(T) + (size_t)nw * nr * mp * sizeof(T);
   o += 2 * (size_t)nt;
   o = (o + 15) & ~(size_t)15;
@@ -326,7 +328,8 @@ k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, c
             int64_t stg_stride, int nrhs, int NS, int mpmax, int32_t *status) {
   using T = C<R>;
   constexpr int CT = NW * 32;
-  constexpr int TPC = tiles_per_stage<S>();
+  constexpr int TPW = sym_tiles_per_warp<S>();
+  constexpr int TPC = NW * TPW;   // tiles per ring stage
   constexpr int TE = TB * TB;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const SubDev s = subs[blockIdx.x];
@@ -438,9 +441,6 @@ k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, c
       }
     }
     consumer_sync(CT);
-    T accJ[NR];
-#pragma unroll
-    for (int q = 0; q < NR; ++q) accJ[q] = mk<T>(0, 0);
     T *pw = part + (size_t)warp * NR * mpmax;
     for (int c = 0; c < nck; ++c, ++it) {
       const int slot = (int)(it % NS);
@@ -450,11 +450,12 @@ k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, c
         atomicOr(status, ST_TIMEOUT);
       }
       const S *stage = ring + (size_t)slot * TPC * TE;
-      const int u0 = c * TPC, un = min(TPC, nt - u0);
-      for (int du = 0; du < un; ++du) {
+      const int u0 = c * TPC;
+#pragma unroll
+      for (int t = 0; t < TPW; ++t) {
+        const int du = t * NW + warp;
+        if (u0 + du >= nt) break;
         const int I = tI[u0 + du], J = tJ[u0 + du];
-        const int own = min(J, mt - 1 - J) % NW;
-        if (own != warp) continue;
         const S *tile = stage + du * TE;
         T pr[NR], pc[NR];
 #pragma unroll
@@ -481,22 +482,19 @@ k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, c
           pr[q].y += __shfl_xor_sync(0xffffffffu, pr[q].y, 16);
           pc[q].x += __shfl_xor_sync(0xffffffffu, pc[q].x, 16);
           pc[q].y += __shfl_xor_sync(0xffffffffu, pc[q].y, 16);
-          accJ[q] = cadd(accJ[q], pc[q]);
         }
         if (h == 0) {
 #pragma unroll
           for (int q = 0; q < NR; ++q) {
             T *dst = pw + q * mpmax + I * TB + rr;
             *dst = cadd(*dst, pr[q]);
-            if (I == J) {   // the column is complete
-              T *dj = pw + q * mpmax + J * TB + rr;
-              *dj = cadd(*dj, accJ[q]);
-            }
           }
-        }
-        if (I == J) {
+        } else if (I != J) {
 #pragma unroll
-          for (int q = 0; q < NR; ++q) accJ[q] = mk<T>(0, 0);
+          for (int q = 0; q < NR; ++q) {
+            T *dst = pw + q * mpmax + J * TB + rr;
+            *dst = cadd(*dst, pc[q]);
+          }
         }
       }
       __syncwarp();
@@ -619,7 +617,7 @@ static cudaError_t launch_subst_sym(hd_ctx *ctx, const double2 *r, int nrhs, int
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int per_sm = (int)std::min<int64_t>(7, ((int64_t)ctx->nsub * groups + sms - 1) / sms);
   const size_t fixed = subst_sym_smem<T, S>(0, mpmax, NW, NR, ntmax);
-  const size_t stage = (size_t)tiles_per_stage<S>() * TB * TB * sizeof(S);
+  const size_t stage = (size_t)NW * sym_tiles_per_warp<S>() * TB * TB * sizeof(S);
   const size_t budget = (size_t)200 * 1024 / (size_t)std::max(1, per_sm);
   int ns = ctx->tune_ns > 0 && NR == 1 ? ctx->tune_ns : (budget > fixed ? (int)((budget - fixed) / (stage + 16)) : 2);
   ns = std::min(32, std::max(2, ns));
@@ -726,8 +724,11 @@ int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cud
     }
   }
   const int ldmax = ld_max(ctx);
-  // one ring stage: 8 KB of tiles (symmetric) or chunk_cols<S>() columns of ldmax entries (64 bytes per row)
-  const size_t stage = ctx->sym ? (size_t)8192 : (size_t)ldmax * 64;
+  // one ring stage: NW warps x tiles per warp (symmetric) or chunk_cols<S>() columns of
+  // ldmax entries (64 bytes per row)
+  const size_t sb = store_bytes(ctx->prec);
+  const size_t stage = ctx->sym ? (size_t)(ctx->max_m <= 192 ? 6 : 8) * (sb == 4 ? 2 : 1) * TB * TB * sb
+                                : (size_t)ldmax * 64;
   int dev_optin = 0;
   cudaDeviceGetAttribute(&dev_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   std::vector<int> cts = ctx->sym ? std::vector<int>{ctx->max_m <= 192 ? 192 : 256}

@@ -27,7 +27,7 @@ class HelmholtzDDM:
                  precision: str = "c64", cut_x: Optional[Sequence[int]] = None, cut_y: Optional[Sequence[int]] = None,
                  own_global_pml: bool = True, sigma0_over_omega: float = 20.0, pml_power: int = 2,
                  device: str = "cuda", stream: Optional[torch.cuda.Stream] = None, factor: bool = True,
-                 symmetric: bool = False):
+                 symmetric: bool = True):
         if not torch.cuda.is_available():
             raise RuntimeError("HelmholtzDDM needs a CUDA device: there is no CPU path")
         self.N, self.npml, self.n = N, npml, N + 2 * npml
@@ -146,7 +146,7 @@ class HelmholtzDDM:
 
 def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: int, overlap: int,
                restart: int, rtol: float, max_iters: int = 5000, precision: str = "c64", cut_x=None, cut_y=None,
-               device: str = "cuda", arnoldi: str = "auto", symmetric: bool = False, reorth: str = "selective"):
+               device: str = "cuda", arnoldi: str = "auto", symmetric: bool = True, reorth: str = "selective"):
     """End-to-end solve from host arrays: velocity c [n][n] (float64) and source
     samples f [nrhs][n][n] (complex128), preferably in pinned memory.  Copies in,
     sets up the medium, factorises, forms b = J h^2 f, runs FGMRES and copies the
@@ -173,7 +173,7 @@ class Server:
         self._keep = {}
 
     def submit(self, c, f, N, npml, omega, nbx, nby, overlap, restart, rtol, max_iters=5000, precision="c64",
-               cut_x=None, cut_y=None, arnoldi="auto", symmetric=False, reorth="selective"):
+               cut_x=None, cut_y=None, arnoldi="auto", symmetric=True, reorth="selective"):
         """c: float64 [n][n], f: complex128 [nrhs][n][n] host arrays.  Returns a ticket."""
         c = np.ascontiguousarray(c, dtype=np.float64)
         f = np.ascontiguousarray(f, dtype=np.complex128)
