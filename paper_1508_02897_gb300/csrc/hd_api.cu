@@ -79,6 +79,7 @@ static void free_ctx(hd_ctx *c) {
   }
   if (c->gevent) cudaEventDestroy(c->gevent);
   if (c->d_k2) cudaFreeAsync(c->d_k2, c->stream);
+  if (c->d_cc) cudaFreeAsync(c->d_cc, c->stream);
   if (c->d_gax_c) cudaFreeAsync(c->d_gax_c, c->stream);
   if (c->d_giax_f) cudaFreeAsync(c->d_giax_f, c->stream);
   if (c->d_gay_c) cudaFreeAsync(c->d_gay_c, c->stream);
@@ -200,6 +201,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
     if (e_ != cudaSuccess) { free_ctx(c); return cuda_fail(e_, "cudaMallocAsync"); } \
   } while (0)
   ALLOC(c->d_k2, sizeof(double) * n);
+  ALLOC(c->d_cc, sizeof(double) * n);
   ALLOC(c->d_gax_c, sizeof(double2) * c->NX);
   ALLOC(c->d_giax_f, sizeof(double2) * (c->NX + 1));
   ALLOC(c->d_gay_c, sizeof(double2) * c->NY);

@@ -14,7 +14,11 @@
 // elimination with partial pivoting done implicitly (rows never move: the
 // pivot of step k is the largest unpivoted entry of column k), blocked by
 // panels of PB columns:
-//   1. the panel is eliminated in shared memory, one thread per row;
+//   1. the panel is eliminated with one thread per row (m <= 256 = FT): every
+//      thread keeps its row of the panel in registers, publishes it each step
+//      into one of two shared buffers (alternating), and the pivot of the next
+//      step is found by a block-wide argmax while the current step ends, so a
+//      step costs one barrier;
 //   2. with T the product of the panel's PB elementary steps and p_t its pivot
 //      rows, the eliminated panel column t equals T e_{p_t}, and T leaves
 //      e_i unchanged for every non-pivot row i, so every other column c becomes
@@ -23,21 +27,32 @@
 //      four rows of a tile m/4 apart).
 // If the pivot of step k sits in row p_k and q = p^{-1}, the in-place result W
 // satisfies S^{-1}[r][c] = W[p_r][q_c], which is how the inverse is written out;
-// the same pass builds S_{j+1} from the inverse still in compute precision into
-// the second working matrix, so the stored copy may be narrower (FP16 storage
-// with FP32 arithmetic) without feeding its rounding back into the recursion.
+// when the stored copy is narrower than the arithmetic (FP16 storage with FP32
+// arithmetic) the same pass builds S_{j+1} from the inverse still in compute
+// precision into a second working matrix, so storage rounding never feeds back
+// into the recursion; otherwise S_{j+1} is built at the start of the next row
+// from the stored inverse itself (one working matrix per box, so the working set
+// of all resident boxes stays in L2).
 #include "hd_internal.cuh"
 
 namespace hd {
 
-constexpr int FT = 256;        // threads per CTA (two CTAs, two boxes, share an SM)
+constexpr int FT = 256;        // threads per CTA (one box per CTA)
+// CTAs per SM the register budget is sized for (two: with three or four resident
+// boxes the register cap of 80 or 64 slows the trailing update more than the extra
+// boxes hide latency: 528 / 594 / 556 ms for the 4096^2 factorisation).
+#ifndef FACTOR_CTAS_F32
+#define FACTOR_CTAS_F32 2
+#endif
+template <typename R> constexpr int factor_ctas() { return sizeof(R) == 4 ? FACTOR_CTAS_F32 : 2; }
 constexpr int PB = 16;         // panel width
 constexpr int TR = 4, TC = 4;  // GEMM tile of the trailing update (rows x columns)
 
-// Shared memory: panel [PB][m] | B [PB][m] | lS [m] | X [PB] | IPV [PB] | piv, qinv, mark [m] ints
+// Shared memory: panel [PB][m] | B [PB][m] | lS [m] | piv, qinv, mark [m] ints.  During the
+// panel elimination B is the second buffer of the published rows.
 size_t factor_smem_bytes(int prec, int max_m) {
   size_t cs = compute_bytes(prec);
-  return cs * (2 * (size_t)PB * max_m + max_m + 2 * PB) + sizeof(int) * 3 * (size_t)max_m + 16;
+  return cs * (2 * (size_t)PB * max_m + max_m) + sizeof(int) * 3 * (size_t)max_m + 16;
 }
 
 template <typename T> __device__ __forceinline__ auto cabs2(T a) { return a.x * a.x + a.y * a.y; }
@@ -67,23 +82,48 @@ __device__ __forceinline__ T d_entry(int r, int c, int j, const double2 *a1c, co
   return mk<T>(0, 0);
 }
 
+// Block-wide argmax of v over the CTA (ties: smaller index); every thread gets the
+// result.  sv/si hold one entry per warp; callers alternate two such buffers so a
+// fast warp of the next call cannot overwrite what a slow warp still reads.
+template <typename R>
+__device__ __forceinline__ void block_argmax(R v, int idx, R *sv, int *si, R &best, int &bi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const R ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if (lane == 0) { sv[warp] = v; si[warp] = idx; }
+  __syncthreads();
+  best = sv[0];
+  bi = si[0];
+#pragma unroll
+  for (int w = 1; w < FT / 32; ++w) {
+    const R ov = sv[w];
+    const int oi = si[w];
+    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  }
+}
+
 template <typename R, typename S, bool SYM>
-__global__ void __launch_bounds__(FT, 2)
+__global__ void __launch_bounds__(FT, factor_ctas<R>())
 k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const double *__restrict__ k2, int NX,
          double h2, S *__restrict__ factor, C<R> *__restrict__ work, int32_t *status) {
   using T = C<R>;
+  constexpr bool KEEP2 = sizeof(S) != sizeof(T);   // narrower storage: S_{j+1} kept in W2
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SubDev s = subs[blockIdx.x];
   const int m = s.ex, rows = s.ey;
   T *P = reinterpret_cast<T *>(smem_raw);   // [PB][m] panel (eliminated in place)
   T *Bm = P + PB * m;                        // [PB][m] pivot rows of the other columns
   T *lS = Bm + PB * m;                       // [m] coupling L_j of the current grid row
-  T *X = lS + m;                             // [PB] pivot-row values of the panel
-  T *IPV = X + PB;                           // [PB] reciprocal pivots
-  int *piv = reinterpret_cast<int *>(IPV + PB);  // [m] pivot row of step k
+  int *piv = reinterpret_cast<int *>(lS + m);    // [m] pivot row of step k
   int *qinv = piv + m;                           // [m] step at which row r was pivot
   int *mark = qinv + m;                          // [m] panel start at which row r became pivot (-1: not yet)
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
+  __shared__ R redv[2 * (FT / 32)];
+  __shared__ int redi[2 * (FT / 32)];
   const double2 *a1c = pool + s.aoff;
   const double2 *ia1f = a1c + m;
   const double2 *a2c = ia1f + m + 1;
@@ -104,7 +144,32 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
   __syncthreads();
 
   for (int j = 0; j < rows; ++j) {
-    for (int r = tid; r < m; r += FT) mark[r] = -1;
+    if (!KEEP2 && j > 0) {
+      // S_j = D_j - L_j S_{j-1}^{-1} L_j from the stored inverse of row j-1
+      for (int r = tid; r < m; r += FT) {
+        const double2 l = cmul(a1c[r], ia2f[j]);   // south coupling of row j
+        lS[r] = mk<T>((R)l.x, (R)l.y);
+      }
+      __syncthreads();
+      const S *prev = Fs + (int64_t)(j - 1) * slot_elems;
+      const double *k2row = k2 + (int64_t)(s.ey0 + j) * NX + s.ex0;
+      for (int64_t idx = tid; idx < mm; idx += FT) {
+        const int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
+        T v;
+        if (SYM) {
+          const int a = min(r, c), b = max(r, c), I = a >> 4, J = b >> 4, rr = a & 15, cc = b & 15;
+          v = load_c<T>(prev[(int64_t)(J * (J + 1) / 2 + I) * 256 + cc * 16 + ((rr + cc) & 15)]);
+        } else {
+          v = load_c<T>(prev[(int64_t)c * ldm + r]);
+        }
+        W[idx] = cfms(cmul(lS[r], v), lS[c], d_entry<T, R>(r, c, j, a1c, ia1f, a2c, ia2f, k2row, h2));
+      }
+      __syncthreads();
+    }
+    for (int r = tid; r < m; r += FT) {
+      mark[r] = -1;
+      qinv[r] = 0;   // stays a valid index even if a breakdown repeats a pivot row
+    }
     __syncthreads();
 
     // ---- Gauss-Jordan inversion of W with implicit partial pivoting
@@ -115,53 +180,67 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
         P[idx] = W[(int64_t)(k0 + t) * m + r];
       }
       __syncthreads();
-      // 1. eliminate the panel, one thread per row
-      for (int t = 0; t < nb; ++t) {
-        const int k = k0 + t;
-        if (warp == 0) {
-          R best = (R)-1;
-          int bi = m;
-          for (int r = lane; r < m; r += 32) {
-            if (mark[r] < 0) {
-              const R v = cabs2(P[t * m + r]);
-              if (v > best) { best = v; bi = r; }
-            }
-          }
+      // 1. eliminate the panel, one thread per row (row r = tid)
+      const bool own = tid < m;
+      int mymark = own ? mark[tid] : 0;
+      T rv[PB];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const R ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
-          }
-          const int p = bi < m ? bi : 0;
-          T ip = mk<T>(0, 0);
-          if (best > (R)0 && isfinite(best)) ip = cinv(P[t * m + p]);
-          else if (lane == 0) bad = true;
-          // pivot-row values of every panel column after this step (lanes split the columns)
-          for (int tt = lane; tt < nb; tt += 32) X[tt] = tt == t ? ip : cmul(P[tt * m + p], ip);
-          __syncwarp();
-          if (lane == 0) {
-            piv[k] = p;
-            qinv[p] = k;
-            mark[p] = k0;
-            IPV[t] = ip;
-          }
+      for (int tt = 0; tt < PB; ++tt) rv[tt] = (own && tt < nb) ? P[tt * m + tid] : mk<T>(0, 0);
+      R best;
+      int p;
+      block_argmax<R>((own && mymark < 0) ? cabs2(rv[0]) : (R)-1, own ? tid : m, redv, redi, best, p);
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        if (t >= nb) break;
+        const int k = k0 + t;
+        const T *Pin = (t & 1) ? Bm : P;   // rows as they were before this step
+        T *Pout = (t & 1) ? P : Bm;
+        const bool ok = best > (R)0 && isfinite(best);
+        if (p >= m) p = 0;
+        T ip;   // reciprocal pivot: one division per warp, broadcast by shuffle
+        {
+          T inv = mk<T>(0, 0);
+          if ((tid & 31) == 0 && ok) inv = cinv(Pin[t * m + p]);
+          ip = mk<T>(__shfl_sync(0xffffffffu, inv.x, 0), __shfl_sync(0xffffffffu, inv.y, 0));
         }
-        __syncthreads();
-        const int p = piv[k];
-        const T ip = IPV[t];
-        for (int r = tid; r < m; r += FT) {
-          const T f = P[t * m + r];   // multiplier of row r (column k before the step)
-          for (int tt = 0; tt < nb; ++tt) {
+        if (tid == 0) {
+          if (!ok) bad = true;
+          piv[k] = p;
+          qinv[p] = k;
+        }
+        if (own) {
+          T f = rv[0];   // multiplier of this row (column k before the step)
+#pragma unroll
+          for (int tt = 1; tt < PB; ++tt)
+            if (tt == t) f = rv[tt];
+          const T g = cmul(f, ip);
+#pragma unroll
+          for (int tt = 0; tt < PB; ++tt) {
+            if (tt >= nb) break;
             T nv;
-            if (r == p) nv = X[tt];
-            else if (tt == t) nv = mk<T>(-(f.x * ip.x - f.y * ip.y), -(f.x * ip.y + f.y * ip.x));
-            else nv = cfms(f, X[tt], P[tt * m + r]);
-            P[tt * m + r] = nv;
+            if (tid == p) nv = tt == t ? ip : cmul(Pin[tt * m + p], ip);   // pivot row / pivot
+            else if (tt == t) nv = mk<T>(-g.x, -g.y);
+            else nv = cfms(g, Pin[tt * m + p], rv[tt]);                   // row - f/pivot * pivot row
+            rv[tt] = nv;
+            Pout[tt * m + tid] = nv;
           }
+          if (tid == p) { mymark = k0; mark[tid] = k0; }
         }
-        __syncthreads();
+        if (t + 1 < nb) {
+          R cand = (R)-1;
+#pragma unroll
+          for (int tt = 1; tt < PB; ++tt)
+            if (tt == t + 1) cand = (own && mymark < 0) ? cabs2(rv[tt]) : (R)-1;
+          block_argmax<R>(cand, own ? tid : m, redv + ((t + 1) & 1) * (FT / 32), redi + ((t + 1) & 1) * (FT / 32),
+                          best, p);
+        }
       }
+      __syncthreads();
+      if (own)
+#pragma unroll
+        for (int tt = 0; tt < PB; ++tt)
+          if (tt < nb) P[tt * m + tid] = rv[tt];
+      __syncthreads();
       // 2. write the panel back and gather the pivot rows of the other columns
       const int ncol = m - nb;
       for (int idx = tid; idx < nb * m; idx += FT) {
@@ -215,49 +294,68 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
       __syncthreads();
     }
 
-    // ---- write S_j^{-1}[r][c] = W[p_r][q_c] (column-major) as factor row j and
-    //      build S_{j+1} = D_{j+1} - L_{j+1} S_j^{-1} L_{j+1} from it into W2
-    const bool more = j + 1 < rows;
+    // ---- write S_j^{-1}[r][c] = W[p_r][q_c] as factor row j and build
+    //      S_{j+1} = D_{j+1} - L_{j+1} S_j^{-1} L_{j+1} from it into W2, 16 columns at a
+    //      time: column q_c of W is read contiguously and un-permuted into the shared
+    //      buffer Q[cc][r] = S_j^{-1}[r][c0 + cc], from which the stored tiles (or
+    //      columns) and W2 are written with consecutive threads on consecutive addresses.
+    const bool more = KEEP2 && j + 1 < rows;
     if (more)
       for (int r = tid; r < m; r += FT) {
         const double2 l = cmul(a1c[r], ia2f[j + 1]);   // south coupling of row j+1
         lS[r] = mk<T>((R)l.x, (R)l.y);
       }
-    __syncthreads();
     S *slot = Fs + j * slot_elems;
     const double *k2row = k2 + (int64_t)(s.ey0 + j + 1) * NX + s.ex0;
-    if (SYM) {
-      // upper 16 x 16 tiles of the exactly symmetric matrix S^{-1}[min(r,c)][max(r,c)],
-      // tile (I, J) at J(J+1)/2 + I, entry (r, c) at c*16 + ((r + c) & 15)
-      const int mt = (m + 15) / 16;
-      const int64_t ntile = (int64_t)mt * (mt + 1) / 2;
-      for (int64_t idx = tid; idx < ntile * 256; idx += FT) {
-        const int u = (int)(idx >> 8), e = (int)(idx & 255);
-        int J = 0;
-        while ((J + 1) * (J + 2) / 2 <= u) ++J;
-        const int I = u - J * (J + 1) / 2;
-        const int cc = e >> 4, rr = ((e & 15) - cc) & 15;
-        const int r = I * 16 + rr, c = J * 16 + cc;
-        T v = mk<T>(0, 0);
-        if (r < m && c < m) v = W[(int64_t)qinv[max(r, c)] * m + piv[min(r, c)]];
-        slot[idx] = store_c<S>(v);
+    T *Q = P;
+    const int mt = (m + 15) / 16;
+    for (int J = 0; J < mt; ++J) {
+      const int c0 = 16 * J, nc = min(16, m - c0);
+      __syncthreads();   // the previous block's reads of Q are done
+      for (int idx = tid; idx < nc * m; idx += FT) {
+        const int cc = idx / m, i = idx - cc * m;
+        Q[cc * m + qinv[i]] = W[(int64_t)qinv[c0 + cc] * m + i];
       }
-      if (more)
-        for (int64_t idx = tid; idx < mm; idx += FT) {
-          const int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
-          const T v = W[(int64_t)qinv[max(r, c)] * m + piv[min(r, c)]];
-          W2[idx] = cfms(cmul(lS[r], v), lS[c], d_entry<T, R>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
+      __syncthreads();
+      if (SYM) {
+        // upper 16 x 16 tiles (I, J), I <= J, of the exactly symmetric matrix
+        // S^{-1}[min(r,c)][max(r,c)]: tile at J(J+1)/2 + I, entry (r, c) at c*16 + ((r + c) & 15)
+        S *tiles = slot + (int64_t)(J * (J + 1) / 2) * 256;
+        for (int e2 = tid; e2 < (J + 1) * 256; e2 += FT) {
+          const int I = e2 >> 8, e = e2 & 255;
+          const int cc = e >> 4, rr = ((e & 15) - cc) & 15;
+          const int r = I * 16 + rr, c = c0 + cc;
+          T v = mk<T>(0, 0);
+          if (r < m && c < m) v = r <= c ? Q[cc * m + r] : Q[(r - c0) * m + c];
+          tiles[e2] = store_c<S>(v);
         }
-    } else {
-      for (int64_t idx = tid; idx < mm; idx += FT) {
-        const int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
-        const T v = W[(int64_t)qinv[c] * m + piv[r]];
-        slot[(int64_t)c * ldm + r] = store_c<S>(v);
-        if (more) W2[idx] = cfms(cmul(lS[r], v), lS[c], d_entry<T, R>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
+        if (more) {
+          // entries (r, c), r <= c, of the block's columns ...
+          for (int idx = tid; idx < nc * m; idx += FT) {
+            const int cc = idx / m, r = idx - cc * m, c = c0 + cc;
+            if (r <= c)
+              W2[(int64_t)c * m + r] =
+                  cfms(cmul(lS[r], Q[cc * m + r]), lS[c], d_entry<T, R>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
+          }
+          // ... and their mirror images (c, r) below the diagonal
+          for (int idx = tid; idx < 16 * m; idx += FT) {
+            const int cc = idx & 15, r = idx >> 4, c = c0 + cc;
+            if (cc < nc && r < c)
+              W2[(int64_t)r * m + c] =
+                  cfms(cmul(lS[c], Q[cc * m + r]), lS[r], d_entry<T, R>(c, r, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
+          }
+        }
+      } else {
+        for (int idx = tid; idx < nc * m; idx += FT) {
+          const int cc = idx / m, r = idx - cc * m, c = c0 + cc;
+          const T v = Q[cc * m + r];
+          slot[(int64_t)c * ldm + r] = store_c<S>(v);
+          if (more) W2[(int64_t)c * m + r] = cfms(cmul(lS[r], v), lS[c], d_entry<T, R>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
+        }
       }
     }
     __syncthreads();
-    T *tmp = W; W = W2; W2 = tmp;
+    if (KEEP2) { T *tmp = W; W = W2; W2 = tmp; }
   }
   if (bad) atomicOr(status, ST_ZERO_PIVOT);
 }

@@ -132,6 +132,7 @@ struct hd_ctx {
   int64_t factor_elems, staging_elems, work_elems;
   // device tables (owned)
   double *d_k2 = nullptr;
+  double *d_cc = nullptr;   // h^2 k^2 - 4: the centre coefficient of A outside the PML
   double2 *d_gax_c = nullptr, *d_giax_f = nullptr, *d_gay_c = nullptr, *d_giay_f = nullptr;
   double2 *d_lpool = nullptr;   // per-box PML tables: a1c[ex], ia1f[ex+1], a2c[ey], ia2f[ey+1]
   hd::SubDev *d_subs = nullptr;

@@ -98,7 +98,7 @@ static size_t request_bytes(const Request &q, int batch) {
       work += 2 * (size_t)b * b;
     }
   const size_t n = (size_t)(q.grid.nx + 2 * q.grid.npml) * (q.grid.ny + 2 * q.grid.npml);
-  const size_t tables = n * 8 + ((size_t)1 << 20);
+  const size_t tables = 2 * n * 8 + ((size_t)1 << 20);   // k^2, centre coefficients, PML tables
   const size_t vecs = n * 8 + 2 * n * 16 * (size_t)batch;     // velocity, right-hand sides, solutions
   return store_bytes(q.precision & 0xff) * factor + cs * std::max(staging * batch, work) + krylov_bytes((int64_t)n, q.opts.restart, batch) +
          tables + vecs;

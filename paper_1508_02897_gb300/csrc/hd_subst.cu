@@ -528,33 +528,46 @@ k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, c
   }
 }
 
+// The sum runs in the compute precision of the local solutions (FP32 for the c64
+// modes: one conversion per cell instead of one per contribution, since the FP64
+// pipe is the scarce one on this GPU) and is written out as complex128.
 template <typename R>
 __global__ void __launch_bounds__(256)
 k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const AxisDev *__restrict__ axy,
          const int32_t *__restrict__ nearx, const int32_t *__restrict__ neary, int nbx, int nby,
          const C<R> *__restrict__ staging_all, int64_t stg_stride, double2 *__restrict__ z_all, int64_t vec_stride,
          int NX) {
-  int gx = blockIdx.x * blockDim.x + threadIdx.x;
-  int gy = blockIdx.y;
+  __shared__ int ylist[3], yoff[3], ny_s;
+  const int gy = blockIdx.y;
+  if (threadIdx.x == 0) {
+    // boxes whose extent covers grid row gy (at most 3, in practice 1 or 2)
+    const int iy = neary[gy];
+    int cnt = 0;
+    for (int jy = max(iy - 1, 0); jy <= min(iy + 1, nby - 1); ++jy) {
+      const AxisDev ay = axy[jy];
+      if (gy >= ay.e0 && gy < ay.e1) { ylist[cnt] = jy; yoff[cnt] = gy - ay.e0; ++cnt; }
+    }
+    ny_s = cnt;
+  }
+  __syncthreads();
+  const int gx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gx >= NX) return;
   const C<R> *staging = staging_all + (int64_t)blockIdx.z * stg_stride;
   double2 *z = z_all + (int64_t)blockIdx.z * vec_stride;
-  if (gx >= NX) return;
-  const int ix = nearx[gx], iy = neary[gy];
-  double2 acc = make_double2(0.0, 0.0);
-  for (int jy = max(iy - 1, 0); jy <= min(iy + 1, nby - 1); ++jy) {
-    const AxisDev ay = axy[jy];
-    if (gy < ay.e0 || gy >= ay.e1) continue;
-    for (int jx = max(ix - 1, 0); jx <= min(ix + 1, nbx - 1); ++jx) {
+  const int ix = nearx[gx];
+  const int jx0 = max(ix - 1, 0), jx1 = min(ix + 1, nbx - 1);
+  C<R> acc = mk<C<R>>(0, 0);
+  for (int q = 0; q < ny_s; ++q) {
+    const int jy = ylist[q], ry = yoff[q];
+    for (int jx = jx0; jx <= jx1; ++jx) {
       const AxisDev ax = axx[jx];
       if (gx < ax.e0 || gx >= ax.e1) continue;
-      const int64_t base = subs[jy * nbx + jx].soff;
       const int ex = ax.e1 - ax.e0;
-      const C<R> v = staging[base + (int64_t)(gy - ay.e0) * ex + (gx - ax.e0)];
-      acc.x += (double)v.x;
-      acc.y += (double)v.y;
+      const C<R> v = staging[subs[jy * nbx + jx].soff + (int64_t)ry * ex + (gx - ax.e0)];
+      acc = cadd(acc, v);
     }
   }
-  z[(int64_t)gy * NX + gx] = acc;
+  z[(int64_t)gy * NX + gx] = make_double2((double)acc.x, (double)acc.y);
 }
 
 // Ring depth: as deep as shared memory allows for the CTAs that share an SM.
