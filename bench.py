@@ -64,8 +64,9 @@ def parse():
     p.add_argument("--reorth", default="selective", choices=("always", "selective"),
                    help="second Gram-Schmidt pass always (CGS2) or only after a cancellation")
     p.add_argument("--no-autotune", dest="autotune", action="store_false")
-    p.add_argument("--storage", default="sym", choices=("sym", "full"),
-                   help="S_j^{-1} storage: upper 16x16 tiles only (sym, default) or full blocks")
+    p.add_argument("--storage", default="auto", choices=("auto", "sym", "full", "tc"),
+                   help="S_j^{-1} storage: upper 16x16 tiles (sym), full blocks, or TF32 planes for the "
+                        "tensor-core substitution (tc); auto: tc for lockstep groups of 8 or more sources, else sym")
     p.add_argument("--symmetric", dest="storage", action="store_const", const="sym", help="same as --storage sym")
     p.add_argument("--full-blocks", dest="storage", action="store_const", const="full", help="same as --storage full")
     p.add_argument("--overlap", type=int, default=None, help="extra overlap lo in cells (default 8)")
@@ -197,21 +198,26 @@ def _rhs_per_cta(k):
     return 8 if k >= 8 else (4 if k >= 4 else (2 if k >= 2 else 1))
 
 
-def block_entries(m: int, sym: bool) -> int:
-    """Stored entries of one S_j^{-1}: m^2, or the upper 16x16 tiles only."""
-    if not sym:
+def block_entries(m: int, storage) -> int:
+    """Stored entries of one S_j^{-1}: m^2 (full), the upper 16x16 tiles (sym), or
+    (m rounded up to 8)^2 (tc)."""
+    if storage == "tc":
+        mp8 = -(-m // 8) * 8
+        return mp8 * mp8
+    if storage in (False, "full"):
         return m * m
     mt = -(-m // 16)
     return mt * (mt + 1) // 2 * 256
 
 
-def subst_bytes(wl, cs: int, nrhs: int = 1, fs: int = None, sym: bool = False) -> int:
+def subst_bytes(wl, cs: int, nrhs: int = 1, fs: int = None, sym=False) -> int:
     """Algorithmic HBM bytes of one substitution launch (one preconditioner
     application to nrhs vectors): every stored S_j^{-1} read once forward and once
     backward (the last row once) per group of right-hand sides sharing a CTA, the
     owned residual read once (FP64 complex), the staging vector written forward,
     read and rewritten backward."""
-    groups = -(-nrhs // _rhs_per_cta(nrhs))
+    per_cta = 16 if sym == "tc" else _rhs_per_cta(nrhs)
+    groups = -(-nrhs // per_cta)
     tot = 16 * wl.n * wl.n * nrhs
     for iy in range(wl.nby):
         for ix in range(wl.nbx):
@@ -246,13 +252,16 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.current_stream(dev)
 
     group = max(1, min(args.group, wl.nrhs))
+    if args.storage == "auto":   # tensor cores pay once a lockstep group is wide enough
+        args.storage = "tc" if group >= 8 and args.precision == "c64" else "sym"
 
-    def one_solve(precision, profile, f=None, grp=None):
+    def one_solve(precision, profile, f=None, grp=None, storage=None):
         f = f_d if f is None else f
         grp = group if grp is None else grp
+        storage = storage or args.storage
         s = HelmholtzDDM(wl.N, wl.npml, wl.omega, c_d, wl.nbx, wl.nby, wl.overlap, precision=precision,
                          cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev),
-                         symmetric=args.storage == "sym")
+                         symmetric=storage == "sym", tcore=storage == "tc" and precision == "c64")
         s.set_profiling(profile)
         s.factor()
         if args.autotune:
@@ -300,7 +309,7 @@ def run_ours(args, world, rank, local):
     launches = int(sum(cls_n.values()))
     cs = 16 if args.precision == "c128" else 8                       # staging (compute) entry
     fs = {"c128": 16, "c64": 8, "c64h": 4}[args.precision]          # stored factor entry
-    sym = args.storage == "sym"
+    sym = args.storage
     sb = subst_bytes(wl, cs, group, fs, sym)
     sub_avg_ms = cls_ms["subst"] / max(cls_n["subst"], 1)
     achieved = sb / (sub_avg_ms / 1e3) / 1e9
@@ -335,13 +344,15 @@ def run_ours(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_max_s * 1e3 / args.steps,
         "sources_per_step": wl.nrhs, "lockstep_group": group,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"c64": "c64+f64", "c64h": "c32(storage)/c64+f64", "c128": "f64"}[args.precision],
+        "dtype": ("tf32(factor storage, tensor-core products)/c64+f64" if args.storage == "tc" else
+                  {"c64": "c64+f64", "c64h": "c32(storage)/c64+f64", "c128": "f64"}[args.precision]),
         "data": "synthetic (seeded random medium and Gaussian source; no dataset)",
         "config": {"workload": describe(wl, args.precision), "N": wl.N, "npml": wl.npml, "boxes": [wl.nbx, wl.nby],
                    "overlap": wl.overlap, "restart": wl.restart, "rtol": wl.rtol, "precision": args.precision,
                    "omega": wl.omega, "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)" % (
                        _factor_gb(wl, fs, sym), 2 * (wl.restart + 1) * n_unk * 16 / 1e9),
-                   "factor_storage": "upper 16x16 tiles (symmetric)" if sym else "full blocks",
+                   "factor_storage": {"sym": "upper 16x16 tiles (symmetric)", "full": "full blocks",
+                                      "tc": "TF32 real/imag planes, tensor-core operand layout"}[sym],
                    "parallelism": f"replicas x{world} (one independent solve per GPU)"},
         "unknown_iters_per_s": unk_iters,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -355,7 +366,8 @@ def run_ours(args, world, rank, local):
                              "mode": args.reorth},
         "breakdown_ms_per_step": {c: cls_ms[c] / args.steps for c in classes},
         "dominant_kernel_class": dominant,
-        "roofline": {"kernel": ("k_subst_sym" if sym else "k_subst") + " (restrict + forward/back substitution)",
+        "roofline": {"kernel": {"sym": "k_subst_sym", "tc": "k_subst_tc", "full": "k_subst"}[sym]
+                               + " (restrict + forward/back substitution)",
                      "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_src, "bytes_per_launch": sb,
@@ -376,13 +388,13 @@ def run_ours(args, world, rank, local):
         e0.record(stream)
         sst = []
         for q in range(args.single_sample):
-            _, st1, _ = one_solve(args.precision, False, f=f_d[q:q + 1], grp=1)
+            _, st1, _ = one_solve(args.precision, False, f=f_d[q:q + 1], grp=1, storage="sym")
             sst.extend(st1)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         t1 = e0.elapsed_time(e1) / 1e3
         out["single_source_solves"] = {"value": args.single_sample / t1, "unit": "solves/s",
-                                       "note": "same workload, one source per solve (factorisation each time)",
+                                       "note": "same workload, one source per solve (factorisation each time, symmetric storage)",
                                        "iters": [x["iters"] for x in sst],
                                        "speedup_of_lockstep_groups": out["value"] / (args.single_sample / t1)}
 
@@ -424,7 +436,7 @@ def run_ours(args, world, rank, local):
             _, _, h2d, d2h = solve_host(c_h, f_h, wl.N, wl.npml, wl.omega, wl.nbx, wl.nby, wl.overlap, wl.restart,
                                         wl.rtol, args.max_iters, precision=args.precision, cut_x=wl.cut_x,
                                         cut_y=wl.cut_y, device=str(dev), arnoldi=args.arnoldi, reorth=args.reorth,
-                                        symmetric=args.storage == "sym")
+                                        symmetric=args.storage == "sym", tcore=args.storage == "tc")
         torch.cuda.synchronize(dev)
         te = max_over_ranks(time.perf_counter() - t0, world)
         out["e2e"] = {"value": world * args.e2e_steps / te, "unit": "solves/s", "h2d_bytes_per_step": h2d,
@@ -465,14 +477,16 @@ def _factor_gb(wl, cs, sym=False):
 def _profile_traffic(wl, args):
     """DRAM bytes per k_subst launch from the committed ncu summary, scaled to
     this workload, when it matches the current kernel (else None)."""
+    if args.storage == "tc":
+        return None
     name = "k_subst_sym_traffic.json" if args.storage == "sym" else "k_subst_traffic.json"
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     try:
         d = json.load(open(path))
-        sym = args.storage == "sym"
-        if (d.get("precision") != args.precision or d.get("kernel_rev") != KERNEL_REV[sym]
+        sym = args.storage
+        if (d.get("precision") != args.precision or d.get("kernel_rev") != KERNEL_REV[sym == "sym"]
                 or d.get("storage", "full") != args.storage):
             return None
         cs = 16 if args.precision == "c128" else 8
@@ -517,7 +531,8 @@ def run_serving(args, world, rank, local):
         if t_arr > now:
             time.sleep(t_arr - now)
         tickets.append((srv.submit(wl.c, wl.f, wl.N, wl.npml, wl.omega, wl.nbx, wl.nby, wl.overlap, wl.restart,
-                                   wl.rtol, args.max_iters, symmetric=args.storage == "sym",
+                                   wl.rtol, args.max_iters, symmetric=args.storage in ("sym", "auto"),
+                                   tcore=args.storage == "tc",
                                    reorth=args.reorth), wl))
     lat, solves, ok, unk_it = [], 0, 0, 0.0
     for t, wl in tickets:

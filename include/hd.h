@@ -62,6 +62,15 @@ typedef enum {
  * computed inverse's upper triangle. */
 #define HD_SYMMETRIC 0x100
 
+/* Flag OR-ed into HD_C64 (not with HD_SYMMETRIC): store every S_j^{-1} rounded to
+ * TF32 as real and imaginary planes in the operand layout of the tensor cores, and
+ * run each substitution step Y = S_j^{-1} V for groups of 16 right-hand sides as
+ * tcgen05 TF32 MMAs with FP32 accumulation ([Yr | Yi] = Sr [Vr | Vi] + Si [-Vi | Vr]).
+ * Meant for many sources sharing one medium (the factor is read once per group of
+ * 16 instead of once per 8); storage is m rounded up to 8, squared, 8 bytes per
+ * entry.  The factorisation itself stays FP32; only the stored copy is TF32. */
+#define HD_TCORE 0x200
+
 /* Truncated domain Omega of Sec. 2: interior nx x ny cells of width h (the
  * interior is [0, nx h] x [0, ny h]), npml PML cells per side.  The PML uses
  * alpha(xi) = 1 + i sigma(xi)/omega with sigma(xi)/omega =

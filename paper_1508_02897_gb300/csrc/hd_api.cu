@@ -151,8 +151,11 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   if (dec->nbx < 1 || dec->nby < 1 || dec->overlap < 0 || dec->nbx > grid->nx || dec->nby > grid->ny)
     return invalid("hd_setup_medium: bad decomposition");
   const int base_prec = precision & 0xff;
-  if ((base_prec != HD_C128 && base_prec != HD_C64 && base_prec != HD_C64_H) || (precision & ~(0xff | HD_SYMMETRIC)))
+  if ((base_prec != HD_C128 && base_prec != HD_C64 && base_prec != HD_C64_H) ||
+      (precision & ~(0xff | HD_SYMMETRIC | HD_TCORE)))
     return invalid("hd_setup_medium: bad precision");
+  if ((precision & HD_TCORE) && (base_prec != HD_C64 || (precision & HD_SYMMETRIC)))
+    return invalid("hd_setup_medium: HD_TCORE needs HD_C64 and excludes HD_SYMMETRIC");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   hd_ctx *c = new (std::nothrow) hd_ctx();
   if (!c) { set_error("hd_setup_medium: host allocation failed"); return HD_ERR_OOM; }
@@ -161,6 +164,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   c->h = grid->h; c->omega = grid->omega; c->s0 = grid->sigma0_over_omega; c->power = grid->pml_power;
   c->prec = base_prec;
   c->sym = (precision & HD_SYMMETRIC) != 0;
+  c->tc = (precision & HD_TCORE) != 0;
   c->stream = st;
   c->nbx = dec->nbx; c->nby = dec->nby; c->overlap = dec->overlap; c->own_global_pml = dec->own_global_pml ? 1 : 0;
   std::vector<int32_t> nearx, neary;
@@ -182,7 +186,10 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
       s.ldm = (s.ex + 3) & ~3;
       s.pad_ = 0;
       const int64_t mt = (s.ex + 15) / 16;
-      s.foff = foff; foff += c->sym ? (int64_t)s.ey * (mt * (mt + 1) / 2) * 256 : (int64_t)s.ey * s.ex * s.ldm;
+      const int64_t mp8 = (s.ex + 7) & ~7;
+      s.foff = foff;
+      foff += c->sym ? (int64_t)s.ey * (mt * (mt + 1) / 2) * 256
+                     : (c->tc ? (int64_t)s.ey * mp8 * mp8 : (int64_t)s.ey * s.ex * s.ldm);
       s.soff = soff; soff += (int64_t)s.ex * s.ey;
       s.woff = woff; woff += 2 * (int64_t)s.ex * s.ex;
       s.aoff = aoff; aoff += 2 * s.ex + 2 * s.ey + 2;

@@ -106,12 +106,24 @@ __device__ __forceinline__ void block_argmax(R v, int idx, R *sv, int *si, R &be
   }
 }
 
-template <typename R, typename S, bool SYM>
+// Storage layouts of the S_j^{-1}: full column-major blocks, upper 16 x 16 tiles,
+// or TF32 real/imaginary planes in the tensor-core operand layout (HD_TCORE).
+enum { LAY_FULL = 0, LAY_SYM = 1, LAY_TC = 2 };
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+template <typename R, typename S, int LAY>
 __global__ void __launch_bounds__(FT, factor_ctas<R>())
 k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const double *__restrict__ k2, int NX,
          double h2, S *__restrict__ factor, C<R> *__restrict__ work, int32_t *status) {
   using T = C<R>;
-  constexpr bool KEEP2 = sizeof(S) != sizeof(T);   // narrower storage: S_{j+1} kept in W2
+  constexpr bool SYM = LAY == LAY_SYM, TCL = LAY == LAY_TC;
+  // S_{j+1} is kept in W2 when the stored copy is narrower than the arithmetic
+  constexpr bool KEEP2 = sizeof(S) != sizeof(T) || TCL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const SubDev s = subs[blockIdx.x];
   const int m = s.ex, rows = s.ey;
@@ -133,7 +145,9 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
   S *Fs = factor + s.foff;
   const int ldm = s.ldm;
   const int64_t mt16 = (m + 15) / 16;
-  const int64_t mm = (int64_t)m * m, slot_elems = SYM ? mt16 * (mt16 + 1) / 2 * 256 : (int64_t)m * ldm;
+  const int mp8 = (m + 7) & ~7;
+  const int64_t mm = (int64_t)m * m;
+  const int64_t slot_elems = SYM ? mt16 * (mt16 + 1) / 2 * 256 : (TCL ? (int64_t)mp8 * mp8 : (int64_t)m * ldm);
   bool bad = false;
 
   // ---- S_0 = D_0
@@ -349,8 +363,27 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
         for (int idx = tid; idx < nc * m; idx += FT) {
           const int cc = idx / m, r = idx - cc * m, c = c0 + cc;
           const T v = Q[cc * m + r];
-          slot[(int64_t)c * ldm + r] = store_c<S>(v);
+          if (!TCL) slot[(int64_t)c * ldm + r] = store_c<S>(v);
           if (more) W2[(int64_t)c * m + r] = cfms(cmul(lS[r], v), lS[c], d_entry<T, R>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
+        }
+        if (TCL) {
+          // chunks 2J, 2J+1 (8 columns each) of the block, each the real then the imaginary
+          // plane [mp8/8 row groups][2 core matrices along K][8 rows][4 columns], TF32
+          float *F = reinterpret_cast<float *>(slot);
+          const int per = 8 * mp8;   // floats of one plane of one chunk
+          for (int idx = tid; idx < 4 * per; idx += FT) {
+            const int cp = idx / per, w = idx - cp * per;
+            const int ch = 2 * J + (cp >> 1), P = cp & 1;
+            if (ch >= mp8 / 8) continue;
+            const int g = w >> 6, kk = (w >> 5) & 1, rr = (w >> 2) & 7, c4 = w & 3;
+            const int r = 8 * g + rr, c = 8 * ch + 4 * kk + c4;
+            float v = 0.f;
+            if (r < m && c < m) {
+              const T q = Q[(c - c0) * m + r];
+              v = tf32_round((float)(P ? q.y : q.x));
+            }
+            F[(int64_t)ch * 2 * per + (int64_t)P * per + w] = v;
+          }
         }
       }
     }
@@ -360,12 +393,12 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
   if (bad) atomicOr(status, ST_ZERO_PIVOT);
 }
 
-template <typename R, typename S, bool SYM>
+template <typename R, typename S, int LAY>
 static cudaError_t launch_factor_rs(hd_ctx *ctx, void *factor, void *work, cudaStream_t st) {
   const size_t smem = factor_smem_bytes(ctx->prec, ctx->max_m);
-  cudaError_t e = cudaFuncSetAttribute(k_factor<R, S, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_factor<R, S, LAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_factor<R, S, SYM><<<ctx->nsub, FT, smem, st>>>(ctx->d_subs, ctx->d_lpool, ctx->d_k2, ctx->NX, ctx->h * ctx->h,
+  k_factor<R, S, LAY><<<ctx->nsub, FT, smem, st>>>(ctx->d_subs, ctx->d_lpool, ctx->d_k2, ctx->NX, ctx->h * ctx->h,
                                              reinterpret_cast<S *>(factor), reinterpret_cast<C<R> *>(work),
                                              ctx->d_status);
   return cudaGetLastError();
@@ -373,12 +406,14 @@ static cudaError_t launch_factor_rs(hd_ctx *ctx, void *factor, void *work, cudaS
 
 template <typename R, typename S>
 static cudaError_t launch_factor_r(hd_ctx *ctx, void *factor, void *work, cudaStream_t st) {
-  return ctx->sym ? launch_factor_rs<R, S, true>(ctx, factor, work, st) : launch_factor_rs<R, S, false>(ctx, factor, work, st);
+  if (ctx->sym) return launch_factor_rs<R, S, LAY_SYM>(ctx, factor, work, st);
+  return launch_factor_rs<R, S, LAY_FULL>(ctx, factor, work, st);
 }
 
 int run_factor(hd_ctx *ctx, void *factor, void *work, cudaStream_t st) {
   tic(ctx, T_FACTOR, st);
-  cudaError_t e = ctx->prec == HD_C64    ? launch_factor_r<float, float2>(ctx, factor, work, st)
+  cudaError_t e = ctx->tc                ? launch_factor_rs<float, float2, LAY_TC>(ctx, factor, work, st)
+                  : ctx->prec == HD_C64  ? launch_factor_r<float, float2>(ctx, factor, work, st)
                   : ctx->prec == HD_C64_H ? launch_factor_r<float, __half2>(ctx, factor, work, st)
                                           : launch_factor_r<double, double2>(ctx, factor, work, st);
   toc(ctx, T_FACTOR, st, 1);

@@ -123,6 +123,7 @@ struct hd_ctx {
   int power;
   int prec;
   bool sym = false;   // S_j^{-1} stored as upper 16 x 16 tiles (HD_SYMMETRIC)
+  bool tc = false;    // S_j^{-1} stored in the tensor-core operand layout (HD_TCORE)
   // decomposition
   int nbx, nby, overlap, own_global_pml;
   int nsub;
@@ -185,6 +186,9 @@ int run_factor(hd_ctx *ctx, void *factor, void *work, cudaStream_t st);
 // staging buffer holds nrhs per-RHS staging vectors of staging_elems entries.
 int run_apply(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs, void *staging,
               cudaStream_t st);
+// Restrict + forward/back substitution on the tensor cores (HD_TCORE storage), staging out.
+cudaError_t launch_subst_tc(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec_stride, void *staging,
+                            int64_t stg_stride, cudaStream_t st);
 size_t krylov_bytes(int64_t n, int restart, int nrhs);
 int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st, int *ct_out,
                    int *ns_out, float *ms_out);

@@ -93,7 +93,9 @@ static size_t request_bytes(const Request &q, int batch) {
   for (int a : ey)
     for (int b : ex) {
       const size_t mt = (b + 15) / 16;
-      factor += sym ? (size_t)a * mt * (mt + 1) / 2 * 256 : (size_t)a * b * ((b + 3) & ~3);
+      const size_t mp8 = (b + 7) & ~7;
+      factor += sym ? (size_t)a * mt * (mt + 1) / 2 * 256
+                    : ((q.precision & HD_TCORE) ? (size_t)a * mp8 * mp8 : (size_t)a * b * ((b + 3) & ~3));
       staging += (size_t)a * b;
       work += 2 * (size_t)b * b;
     }

@@ -659,10 +659,11 @@ static cudaError_t launch_subst_sym_nr(hd_ctx *ctx, const double2 *r, int nrhs, 
 template <typename R, typename S>
 static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs,
                                   void *staging, cudaStream_t st) {
-  if (ctx->sym) {
+  if (ctx->tc || ctx->sym) {
     tic(ctx, T_SUBST, st);
-    cudaError_t e = ctx->max_m <= 192 ? launch_subst_sym_nr<R, S, 6>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
-                                      : launch_subst_sym_nr<R, S, 8>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st);
+    cudaError_t e = ctx->tc ? launch_subst_tc(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
+                    : ctx->max_m <= 192 ? launch_subst_sym_nr<R, S, 6>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
+                                        : launch_subst_sym_nr<R, S, 8>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st);
     toc(ctx, T_SUBST, st, 1);
     if (e != cudaSuccess) return e;
     dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
@@ -721,6 +722,12 @@ static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune
 
 int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st, int *ct_out,
                    int *ns_out, float *ms_out) {
+  if (ctx->tc) {   // the tensor-core substitution has one launch shape (ring sized by shared memory)
+    if (ct_out) *ct_out = 128;
+    if (ns_out) *ns_out = 0;
+    if (ms_out) *ms_out = -1.f;
+    return HD_OK;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   const auto key = std::make_tuple(ctx->prec, ctx->sym ? 1 : 0, ctx->max_m, ctx->nsub, dev);

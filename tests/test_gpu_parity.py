@@ -49,12 +49,13 @@ def oracle(name, own=True):
 
 
 def gpu(name, precision, own=True):
-    """precision: c128 / c64 / c64h, with a trailing "s" for symmetric tile storage."""
+    """precision: c128 / c64 / c64h, with a trailing "s" for symmetric tile storage or
+    "t" for the tensor-core storage (c64t: TF32 factors, tcgen05 substitution)."""
     case, c, g, _, _ = oracle(name, own)
-    sym = precision.endswith("s")
+    sym, tc = precision.endswith("s"), precision.endswith("t")
     return HelmholtzDDM(case["N"], case["npml"], g.omega, c, case["nb"], case["nb"], case["overlap"],
-                        precision=precision.rstrip("s"), cut_x=cuts(case), cut_y=cuts(case), own_global_pml=own,
-                        symmetric=sym)
+                        precision=precision.rstrip("st"), cut_x=cuts(case), cut_y=cuts(case), own_global_pml=own,
+                        symmetric=sym, tcore=tc)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -73,7 +74,7 @@ def test_matvec_and_rhs(name):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4), ("c64h", 3e-2), ("c128s", 1e-10),
-                                           ("c64s", 2e-4), ("c64hs", 3e-2)])
+                                           ("c64s", 2e-4), ("c64hs", 3e-2), ("c64t", 3e-2)])
 def test_precond_parity(name, precision, tol):
     _, _, g, _, P = oracle(name)
     s = gpu(name, precision)
@@ -129,9 +130,9 @@ def test_gmres_converged_c128(name, arnoldi, reorth):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("precision", ["c64", "c64h", "c64s"])
+@pytest.mark.parametrize("precision", ["c64", "c64h", "c64s", "c64t"])
 def test_gmres_mixed_precision(name, precision):
-    """FP32 local factors (stored in FP32 or FP16), FP64 outer loop: the FP64
+    """FP32 local factors (stored in FP32, FP16 or TF32), FP64 outer loop: the FP64
     relative residual reaches the tolerance and the solution matches the FP64
     oracle to 1e-5."""
     case, c, g, A, P = oracle(name)
@@ -168,10 +169,10 @@ def _sources(case, k, seed):
     return np.stack([W.gaussian_source(N, npml, *rng.uniform(0.15, 0.85, 2), 2.0 / N) for _ in range(k)])
 
 
-@pytest.mark.parametrize("precision,nrhs", [("c128", 3), ("c64", 9), ("c64s", 5)])
+@pytest.mark.parametrize("precision,nrhs", [("c128", 3), ("c64", 9), ("c64s", 5), ("c64t", 5), ("c64t", 19)])
 def test_precond_batched_equals_single(precision, nrhs):
-    """Each right-hand side of a batched application (groups of up to 8 per CTA)
-    gives bitwise the same vector as its own application."""
+    """Each right-hand side of a batched application (groups of up to 8 per CTA, 16
+    on the tensor cores) gives bitwise the same vector as its own application."""
     _, _, g, _, P = oracle("ragged")
     s = gpu("ragged", precision)
     r = W.random_complex((nrhs, g.n, g.n), seed=12)
@@ -183,11 +184,11 @@ def test_precond_batched_equals_single(precision, nrhs):
     for k in range(nrhs):
         zk = s.apply_precond(torch.from_numpy(r[k])).cpu().numpy()
         assert np.array_equal(z[k], zk)
-    tol = 1e-10 if precision.startswith("c128") else 2e-4
+    tol = 1e-10 if precision.startswith("c128") else (3e-2 if precision.endswith("t") else 2e-4)
     assert rel(z[nrhs - 1], P.apply(r[nrhs - 1])) < tol
 
 
-@pytest.mark.parametrize("precision", ["c128", "c64"])
+@pytest.mark.parametrize("precision", ["c128", "c64", "c64t"])
 def test_gmres_batched_alone_vs_mix(precision):
     """Lockstep solve of several sources sharing one factorisation: every
     solution is bitwise the one its source gets alone, and matches the oracle."""
