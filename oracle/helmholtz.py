@@ -198,7 +198,9 @@ class DDMPreconditioner:
     def __init__(self, grid: Grid, c: np.ndarray, cut_x, cut_y, overlap: int,
                  own_global_pml: bool = True, subdomains: Optional[Sequence[int]] = None):
         self.grid = grid
-        self.k2 = (grid.omega / np.asarray(c, dtype=np.float64)) ** 2
+        self.c = np.asarray(c, dtype=np.float64)
+        self.k2 = (grid.omega / self.c) ** 2
+        self._A = None
         self.subs = decompose(grid, cut_x, cut_y, overlap, own_global_pml)
         self.active = list(range(len(self.subs))) if subdomains is None else list(subdomains)
         self.lu = {}
@@ -220,6 +222,52 @@ class DDMPreconditioner:
         for s_idx in self.active:
             s = self.subs[s_idx]
             z[s.ey0:s.ey1, s.ex0:s.ex1] += self.local_solve(s_idx, r)
+        return z
+
+    def neighbours(self, s_idx: int) -> List[int]:
+        """The index set N_ij of Sec. 2: the (up to 8) boxes whose i, j differ by at most 1."""
+        s = self.subs[s_idx]
+        return [t for t in self.active if t != s_idx
+                and abs(self.subs[t].i - s.i) <= 1 and abs(self.subs[t].j - s.j) <= 1]
+
+    def apply_multistep(self, f: np.ndarray, steps: int) -> np.ndarray:
+        """The overlapping DDM of Eq. (ddm0), (ddms) and (sum), run for ``steps``
+        steps (steps = 1 is the one-step preconditioner of Eq. (pc)).
+
+        Step 0 solves every box with f restricted to its owned box.  Step s+1
+        solves box ij with minus the sum over its neighbours N_ij of L applied to
+        their step-s solutions (each extended by zero outside its box), restricted
+        to the owned box of ij; L is the operator of the whole truncated domain.
+        The result is the sum of every step's local solutions over their full boxes.
+        """
+        if steps < 1:
+            raise ValueError("steps must be >= 1")
+        g = self.grid
+        if self._A is None:
+            self._A = global_operator(g, self.c)
+        f = np.asarray(f, dtype=np.complex128).reshape(g.n, g.n)
+        z = np.zeros_like(f)
+        u = {}
+        for s_idx in self.active:
+            s = self.subs[s_idx]
+            u[s_idx] = self.local_solve(s_idx, f)
+            z[s.ey0:s.ey1, s.ex0:s.ex1] += u[s_idx]
+        for _ in range(1, steps):
+            Lu = {}
+            for t in self.active:                       # L(u_t^s), u_t^s extended by zero
+                st = self.subs[t]
+                e = np.zeros_like(f)
+                e[st.ey0:st.ey1, st.ex0:st.ex1] = u[t]
+                Lu[t] = (self._A @ e.ravel()).reshape(g.n, g.n)
+            u_next = {}
+            for s_idx in self.active:
+                src = np.zeros_like(f)
+                for t in self.neighbours(s_idx):
+                    src -= Lu[t]
+                s = self.subs[s_idx]
+                u_next[s_idx] = self.local_solve(s_idx, src)    # restricted to the owned box
+                z[s.ey0:s.ey1, s.ex0:s.ex1] += u_next[s_idx]
+            u = u_next
         return z
 
 

@@ -212,6 +212,49 @@ def test_dense_brute_force_preconditioner():
     np.testing.assert_allclose(P.apply(r).ravel(), M @ r, rtol=1e-11, atol=1e-12)
 
 
+# ---------------------------------------------------------------- multi-step DDM
+def _ddm_case():
+    wl = W.make_workload("tiny", N=96, nb=3, medium="three_layer")
+    g = Grid(wl.N, wl.npml, wl.omega)
+    return wl, g, global_operator(g, wl.c), DDMPreconditioner(g, wl.c, wl.cut_x, wl.cut_y, wl.overlap)
+
+
+def test_multistep_equals_residual_correction():
+    """Eq. (ddms) with the Sec. 2 fact that a box's own residual vanishes on its
+    owned part: the step-(s+1) sources are exactly the global residual f - A z_s of
+    the sum so far, restricted to the owned boxes, so s steps of Eq. (ddms) + (sum)
+    equal z_{s+1} = z_s + M (f - A z_s), z_0 = M f (M: Eq. (pc)).  A dropped corner
+    neighbour, a wrong sign or a wrong restriction breaks this."""
+    wl, g, A, P = _ddm_case()
+    f = W.random_complex((g.n, g.n), seed=21)
+    z = P.apply(f)
+    for steps in (1, 2, 3):
+        if steps > 1:
+            z = z + P.apply((f.ravel() - A @ z.ravel()).reshape(g.n, g.n))
+        zs = P.apply_multistep(f, steps)
+        assert np.linalg.norm(zs - z) / np.linalg.norm(z) < 1e-12
+
+
+def test_multistep_solver_converges():
+    """Sec. 2: the iteration goes on until the residual is small; each step carries
+    the waves one more box, so the residual of the DDM sum falls with the steps."""
+    wl, g, A, P = _ddm_case()
+    b = rhs_from_source(g, wl.f[0])
+    res = [np.linalg.norm(b.ravel() - A @ P.apply_multistep(b, k).ravel()) / np.linalg.norm(b) for k in (1, 3, 6)]
+    assert res[1] < 0.5 * res[0] and res[2] < 0.2 * res[0]
+
+
+def test_multistep_one_box_adds_nothing():
+    """With one box there are no neighbours: every step after the first has zero
+    sources, and the sum is the exact solve of the one-box case."""
+    wl = W.make_workload("tiny", N=48, nb=1)
+    g = Grid(wl.N, wl.npml, wl.omega)
+    A = global_operator(g, wl.c)
+    P = DDMPreconditioner(g, wl.c, wl.cut_x, wl.cut_y, wl.overlap)
+    r = W.random_complex((g.n, g.n), seed=13)
+    np.testing.assert_allclose(P.apply_multistep(r, 3).ravel(), _solve(A, r.ravel()), rtol=1e-12, atol=1e-12)
+
+
 # ---------------------------------------------------------------- GMRES
 def test_fgmres_identity_matches_dense_solve():
     rng = np.random.default_rng(0)
