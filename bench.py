@@ -64,6 +64,8 @@ def parse():
     p.add_argument("--reorth", default="selective", choices=("always", "selective"),
                    help="second Gram-Schmidt pass always (CGS2) or only after a cancellation")
     p.add_argument("--no-autotune", dest="autotune", action="store_false")
+    p.add_argument("--precond-steps", type=int, default=1,
+                   help="steps of the overlapping DDM used as the preconditioner (Eq. (ddms); 1: Eq. (pc))")
     p.add_argument("--storage", default="auto", choices=("auto", "sym", "full", "tc"),
                    help="S_j^{-1} storage: upper 16x16 tiles (sym), full blocks, or TF32 planes for the "
                         "tensor-core substitution (tc); auto: tc for lockstep groups of 8 or more sources, else sym")
@@ -270,7 +272,8 @@ def run_ours(args, world, rank, local):
         for g0 in range(0, f.shape[0], grp):
             b = s.rhs(f[g0:g0 + grp])
             x, st = s.solve(b, restart=wl.restart, rtol=wl.rtol, max_iters=args.max_iters,
-                            arnoldi=args.arnoldi if precision == args.precision else "fp64", reorth=args.reorth)
+                            arnoldi=args.arnoldi if precision == args.precision else "fp64", reorth=args.reorth,
+                            precond_steps=args.precond_steps)
             sts.extend(st)
         tm = s.timers(reset=True)
         s.close()
@@ -351,6 +354,7 @@ def run_ours(args, world, rank, local):
                    "overlap": wl.overlap, "restart": wl.restart, "rtol": wl.rtol, "precision": args.precision,
                    "omega": wl.omega, "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)" % (
                        _factor_gb(wl, fs, sym), 2 * (wl.restart + 1) * n_unk * 16 / 1e9),
+                   "precond_steps": args.precond_steps,
                    "factor_storage": {"sym": "upper 16x16 tiles (symmetric)", "full": "full blocks",
                                       "tc": "TF32 real/imag planes, tensor-core operand layout"}[sym],
                    "parallelism": f"replicas x{world} (one independent solve per GPU)"},

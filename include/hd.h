@@ -156,6 +156,20 @@ int hd_rhs_from_source(hd_ctx *ctx, const void *f_dev, void *b_dev, int32_t nrhs
 int hd_apply_precond(hd_ctx *ctx, const void *r_dev, void *z_dev, int32_t nrhs, void *scratch_dev,
                      size_t scratch_bytes, void *stream);
 
+/* Multi-step overlapping DDM, Eq. (ddm0), (ddms) and (sum): u = the sum over
+ * steps s < nsteps of every box's local solution, step 0 with f restricted to the
+ * owned boxes, step s+1 with minus the sum of the neighbours' L u^s restricted to
+ * them (L: the operator of the whole truncated domain).  Since a box's own
+ * residual vanishes on its owned part (Sec. 2), the step-(s+1) sources are the
+ * global residual of the sum so far, and this is computed as
+ *     u_0 = M f,   u_{s+1} = u_s + M (f - A u_s),   M = hd_apply_precond.
+ * nsteps = 1 is hd_apply_precond.  f_dev, u_dev: complex128 [nrhs][NY][NX], u is
+ * the output and must not alias f; work_dev: 2 * nrhs * NX * NY * 16 bytes (the
+ * residual and the correction); scratch as for hd_apply_precond (nrhs vectors
+ * at once).  Asynchronous on stream. */
+int hd_apply_ddm(hd_ctx *ctx, const void *f_dev, void *u_dev, int32_t nrhs, int32_t nsteps, void *work_dev,
+                 size_t work_bytes, void *scratch_dev, size_t scratch_bytes, void *stream);
+
 /* Arithmetic of the Gram-Schmidt dot products and updates. */
 typedef enum {
   HD_ARNOLDI_FP64 = 0,  /* IEEE FP64 throughout                                       */
@@ -195,6 +209,9 @@ typedef struct {
   int32_t reorth;     /* 0: always two Gram-Schmidt passes (CGS2); 1: second pass only
                          when the first cancelled more than a factor 10 of ||w||
                          (Rutishauser's criterion, decided on the device)          */
+  int32_t precond_steps; /* steps of the overlapping DDM used as the preconditioner
+                         (hd_apply_ddm); 0 or 1: the one-step preconditioner of
+                         Eq. (pc)                                                  */
 } hd_gmres_opts;
 
 typedef struct {

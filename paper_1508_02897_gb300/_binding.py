@@ -38,7 +38,8 @@ class hd_decomp(ct.Structure):
 
 class hd_gmres_opts(ct.Structure):
     _fields_ = [("restart", ct.c_int32), ("max_iters", ct.c_int32), ("rtol", ct.c_double), ("use_x0", ct.c_int32),
-                ("arnoldi", ct.c_int32), ("graphs", ct.c_int32), ("reorth", ct.c_int32)]
+                ("arnoldi", ct.c_int32), ("graphs", ct.c_int32), ("reorth", ct.c_int32),
+                ("precond_steps", ct.c_int32)]
 
 
 class hd_gmres_stats(ct.Structure):
@@ -82,6 +83,7 @@ _SIGS = {
     "hd_matvec": [_P, _P, _P, ct.c_int32, _P],
     "hd_rhs_from_source": [_P, _P, _P, ct.c_int32, _P],
     "hd_apply_precond": [_P, _P, _P, ct.c_int32, _P, ct.c_size_t, _P],
+    "hd_apply_ddm": [_P, _P, _P, ct.c_int32, ct.c_int32, _P, ct.c_size_t, _P, ct.c_size_t, _P],
     "hd_gmres_solve": [_P, _P, _P, ct.c_int32, ct.POINTER(hd_gmres_opts), _P, ct.c_size_t, _P, ct.c_size_t,
                        ct.POINTER(hd_gmres_stats), _P],
     "hd_apply_precond_noalloc": [_P, _P, _P, ct.c_int32, _P],
@@ -174,6 +176,11 @@ def hd_apply_precond(ctx, r_ptr, z_ptr, nrhs, scratch_ptr, scratch_bytes, stream
     _check("hd_apply_precond", lib().hd_apply_precond(ctx, r_ptr, z_ptr, nrhs, scratch_ptr, scratch_bytes, stream))
 
 
+def hd_apply_ddm(ctx, f_ptr, u_ptr, nrhs, nsteps, work_ptr, work_bytes, scratch_ptr, scratch_bytes, stream):
+    _check("hd_apply_ddm", lib().hd_apply_ddm(ctx, f_ptr, u_ptr, nrhs, nsteps, work_ptr, work_bytes, scratch_ptr,
+                                              scratch_bytes, stream))
+
+
 def hd_apply_precond_noalloc(ctx, r_ptr, z_ptr, nrhs, stream):
     """Preconditioner application whose staging lives in the library's fixed 64 MiB array
     (for callers that cannot allocate device memory)."""
@@ -182,8 +189,8 @@ def hd_apply_precond_noalloc(ctx, r_ptr, z_ptr, nrhs, stream):
 
 def hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, restart, max_iters, rtol, krylov_ptr, krylov_bytes, scratch_ptr,
                    scratch_bytes, stream, use_x0=0, arnoldi=HD_ARNOLDI_FP64, graphs=0, reorth=0,
-                   raise_on_not_converged=False):
-    o = hd_gmres_opts(restart, max_iters, rtol, use_x0, arnoldi, graphs, reorth)
+                   raise_on_not_converged=False, precond_steps=1):
+    o = hd_gmres_opts(restart, max_iters, rtol, use_x0, arnoldi, graphs, reorth, precond_steps)
     st = (hd_gmres_stats * nrhs)()
     allow = () if raise_on_not_converged else (HD_ERR_NOT_CONVERGED,)
     rc = _check("hd_gmres_solve", lib().hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, ct.byref(o), krylov_ptr, krylov_bytes,
@@ -235,13 +242,13 @@ def hd_server_create(hbm_budget_bytes, max_slots, device=0):
 
 def hd_submit(srv, nx, ny, npml, h, omega, c_ptr, f_ptr, nrhs, precision, restart, max_iters, rtol, x_ptr, nbx, nby,
               overlap, cut_x=None, cut_y=None, own_global_pml=1, arnoldi=HD_ARNOLDI_FP64, sigma0_over_omega=20.0,
-              pml_power=2, reorth=0):
+              pml_power=2, reorth=0, precond_steps=1):
     """Queues a solve; host buffers (c, f, x) must stay alive until hd_poll reports completion."""
     g = hd_grid(nx, ny, npml, h, omega, sigma0_over_omega, pml_power)
     kx, px = _cuts(cut_x)
     ky, py = _cuts(cut_y)
     d = hd_decomp(nbx, nby, overlap, px, py, own_global_pml)
-    o = hd_gmres_opts(restart, max_iters, rtol, 0, arnoldi, 0, reorth)
+    o = hd_gmres_opts(restart, max_iters, rtol, 0, arnoldi, 0, reorth, precond_steps)
     t = ct.c_uint64()
     _check("hd_submit", lib().hd_submit(srv, ct.byref(g), ct.byref(d), c_ptr, f_ptr, nrhs, precision, ct.byref(o),
                                         x_ptr, ct.byref(t)))

@@ -319,12 +319,32 @@ int hd_apply_precond(hd_ctx *c, const void *r, void *z, int32_t nrhs, void *scra
   return HD_OK;
 }
 
+int hd_apply_ddm(hd_ctx *c, const void *f, void *u, int32_t nrhs, int32_t nsteps, void *work, size_t work_bytes,
+                 void *scratch, size_t scratch_bytes, void *stream) {
+  if (!c || !f || !u || !work || !scratch || nrhs < 1 || nsteps < 1) return invalid("hd_apply_ddm: bad argument");
+  if (f == u) return invalid("hd_apply_ddm: u must not alias f");
+  if (!c->factored) return invalid("hd_apply_ddm: call hd_factor_subdomains first");
+  const int64_t n = (int64_t)c->NX * c->NY;
+  if (work_bytes < 2 * sizeof(double2) * (size_t)n * nrhs) {
+    set_error("hd_apply_ddm: work buffer too small (2 * nrhs * NX * NY * 16 bytes)");
+    return HD_ERR_OOM;
+  }
+  if (scratch_bytes < compute_bytes(c->prec) * (size_t)c->staging_elems * nrhs) {
+    set_error("hd_apply_ddm: scratch workspace too small for nrhs right-hand sides");
+    return HD_ERR_OOM;
+  }
+  if (!aligned16(f) || !aligned16(u) || !aligned16(work) || !aligned16(scratch))
+    return invalid("hd_apply_ddm: buffers must be 16-byte aligned");
+  return run_apply_steps(c, reinterpret_cast<const double2 *>(f), n, reinterpret_cast<double2 *>(u), n, nrhs, nsteps,
+                         reinterpret_cast<double2 *>(work), scratch, reinterpret_cast<cudaStream_t>(stream));
+}
+
 int hd_gmres_solve(hd_ctx *c, const void *b, void *x, int32_t nrhs, const hd_gmres_opts *o, void *kws, size_t kbytes,
                    void *scratch, size_t scratch_bytes, hd_gmres_stats *stats, void *stream) {
   if (!c || !b || !x || !o || !kws || !scratch || !stats || nrhs < 1) return invalid("hd_gmres_solve: bad argument");
   if (!c->factored) return invalid("hd_gmres_solve: call hd_factor_subdomains first");
   if (o->restart < 1 || o->max_iters < 0 || !(o->rtol >= 0) || (o->arnoldi != HD_ARNOLDI_FP64 && o->arnoldi != HD_ARNOLDI_DS) ||
-      (o->reorth != 0 && o->reorth != 1))
+      (o->reorth != 0 && o->reorth != 1) || o->precond_steps < 0 || o->precond_steps > 64)
     return invalid("hd_gmres_solve: bad options");
   size_t kb, sb;
   hd_query_workspace(c, nrhs, o->restart, nullptr, &kb, &sb);

@@ -97,7 +97,8 @@ struct AxisDev {
 // A captured Arnoldi step (CUDA graph) and the kernels it holds per timer class.
 struct GraphKey {
   const void *kws, *scratch, *factor;
-  int B, R, mode, j, ct, ns;   // mode: bit 0 double-single Arnoldi, bit 1 selective reorthogonalisation
+  int B, R, mode, j, ct, ns;   // mode: bit 0 double-single Arnoldi, bit 1 selective reorthogonalisation,
+                               // bits 2..: preconditioner steps
   bool operator<(const GraphKey &o) const {
     return std::tie(kws, scratch, factor, B, R, mode, j, ct, ns) <
            std::tie(o.kws, o.scratch, o.factor, o.B, o.R, o.mode, o.j, o.ct, o.ns);
@@ -186,6 +187,13 @@ int run_factor(hd_ctx *ctx, void *factor, void *work, cudaStream_t st);
 // staging buffer holds nrhs per-RHS staging vectors of staging_elems entries.
 int run_apply(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs, void *staging,
               cudaStream_t st);
+// z = sum over nsteps of the multi-step DDM (residual correction around run_apply);
+// work holds 2 * nrhs vectors of NX*NY (residual, correction).
+int run_apply_steps(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs, int nsteps,
+                    double2 *work, void *staging, cudaStream_t st);
+// r = b - A x with strided vectors (nrhs on grid.z)
+cudaError_t launch_residual_strided(hd_ctx *ctx, const double2 *b, int64_t bs, const double2 *x, int64_t xs,
+                                    double2 *r, int64_t rs, int nrhs, cudaStream_t st);
 // Restrict + forward/back substitution on the tensor cores (HD_TCORE storage), staging out.
 cudaError_t launch_subst_tc(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec_stride, void *staging,
                             int64_t stg_stride, cudaStream_t st);

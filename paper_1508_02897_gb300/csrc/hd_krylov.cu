@@ -483,7 +483,7 @@ struct KrylovLayout {
   int64_t n;
   int restart, nrhs, G, Gdf, Gmax;
   size_t off_V, off_Z, off_w, off_vin, off_part, off_h1, off_h2, off_red, off_H, off_cs, off_sn, off_g, off_y,
-      off_stat, off_live, total;
+      off_stat, off_live, off_ddm, total;
 };
 
 static KrylovLayout krylov_layout(int64_t n, int restart, int nrhs) {
@@ -509,6 +509,7 @@ static KrylovLayout krylov_layout(int64_t n, int restart, int nrhs) {
   L.off_y = o; o += al(c16 * R * B);
   L.off_stat = o; o += al(sizeof(double) * 4 * B);
   L.off_live = o; o += al(sizeof(int) * 3 * B);   // live [B], kcnt [B], skip [B]
+  L.off_ddm = o; o += al(c16 * 2 * n * B);       // multi-step DDM: residual and correction
   L.total = o;
   return L;
 }
@@ -701,7 +702,8 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
       const int64_t vjs = dsm ? n : K.ldvr();
       double2 *zj = K.Z() + (int64_t)j * n;
       const int64_t zs = n * R;
-      int rc2 = run_apply(ctx, vj, vjs, zj, zs, B, scratch, st);
+      int rc2 = run_apply_steps(ctx, vj, vjs, zj, zs, B, std::max(1, o->precond_steps), K.at<double2>(K.L.off_ddm),
+                                scratch, st);
       if (rc2) return rc2;
       tic(ctx, T_MATVEC, st);
       KCHK(launch_matvec(ctx, zj, zs, K.w(), n, B, st));
@@ -735,7 +737,9 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
     for (int j = 0; j < R; ++j) {
       if (o->graphs) {
         // each step j is captured once per workspace/launch shape and then replayed
-        const GraphKey key{kws, scratch, ctx->factor, B, R, (dsm ? 1 : 0) | (sel ? 2 : 0), j, ctx->tune_ct, ctx->tune_ns};
+        const GraphKey key{kws,          scratch, ctx->factor, B, R,
+                           (dsm ? 1 : 0) | (sel ? 2 : 0) | (std::max(1, o->precond_steps) << 2), j, ctx->tune_ct,
+                           ctx->tune_ns};
         auto it = ctx->graphs.find(key);
         if (it == ctx->graphs.end()) {
           const bool prof = ctx->profiling;

@@ -147,6 +147,13 @@ cudaError_t launch_residual(hd_ctx *ctx, const double2 *b, const double2 *x, dou
   return cudaGetLastError();
 }
 
+cudaError_t launch_residual_strided(hd_ctx *ctx, const double2 *b, int64_t bs, const double2 *x, int64_t xs,
+                                    double2 *r, int64_t rs, int nrhs, cudaStream_t st) {
+  dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
+  k_stencil<1><<<grid, 256, 0, st>>>(op_args(ctx), x, xs, b, bs, r, rs);
+  return cudaGetLastError();
+}
+
 __global__ void k_rhs(OpArgs a, const double2 *f, double2 *b) {  // b may alias f
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   int j = blockIdx.y;

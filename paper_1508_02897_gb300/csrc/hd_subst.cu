@@ -705,6 +705,37 @@ int run_apply(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs,
   return HD_OK;
 }
 
+// z += c over nrhs strided vectors (grid.y = right-hand side)
+__global__ void k_add(double2 *__restrict__ z, int64_t zs, const double2 *__restrict__ c, int64_t cs, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double2 *zr = z + (int64_t)blockIdx.y * zs;
+  const double2 a = zr[i], b = c[(int64_t)blockIdx.y * cs + i];
+  zr[i] = make_double2(a.x + b.x, a.y + b.y);
+}
+
+// Multi-step overlapping DDM, Eq. (ddm0), (ddms), (sum), as residual correction:
+// z = M r, then nsteps - 1 times  t = r - A z,  z += M t.
+int run_apply_steps(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs, int nrhs, int nsteps,
+                    double2 *work, void *staging, cudaStream_t st) {
+  int rc = run_apply(ctx, r, rs, z, zs, nrhs, staging, st);
+  if (rc || nsteps <= 1) return rc;
+  const int64_t n = (int64_t)ctx->NX * ctx->NY;
+  double2 *t = work, *c = work + n * nrhs;
+  for (int s = 1; s < nsteps; ++s) {
+    tic(ctx, T_MATVEC, st);
+    cudaError_t e = launch_residual_strided(ctx, r, rs, z, zs, t, n, nrhs, st);
+    toc(ctx, T_MATVEC, st, 1);
+    if (e != cudaSuccess) return cuda_fail(e, "multi-step residual");
+    if ((rc = run_apply(ctx, t, n, c, n, nrhs, staging, st))) return rc;
+    tic(ctx, T_GATHER, st);
+    k_add<<<dim3((unsigned)((n + 255) / 256), nrhs), 256, 0, st>>>(z, zs, c, n, n);
+    toc(ctx, T_GATHER, st, 1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "multi-step sum");
+  }
+  return HD_OK;
+}
+
 }  // namespace hd
 
 // ---------------------------------------------------------------------------

@@ -99,6 +99,20 @@ class HelmholtzDDM:
                            self._st())
         return z
 
+    def apply_ddm(self, f, steps: int, out=None):
+        """Multi-step overlapping DDM (hd_apply_ddm): the sum of `steps` rounds of local
+        solves, each round's sources the neighbours' residuals on the owned boxes."""
+        f, nrhs = self._vec(f)
+        u = torch.empty_like(f) if out is None else out
+        work = torch.empty(2 * f.numel() * 16, dtype=torch.uint8, device=self.device)
+        _, _, sb = B.hd_query_workspace(self.ctx, nrhs, 1)
+        if sb > self.scratch_bytes:
+            self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+            self.scratch_bytes = sb
+        B.hd_apply_ddm(self.ctx, f.data_ptr(), u.data_ptr(), nrhs, steps, work.data_ptr(), work.numel(),
+                       self.scratch.data_ptr(), self.scratch_bytes, self._st())
+        return u
+
     def krylov_workspace(self, restart: int, nrhs: int = 1):
         key = (restart, nrhs)
         if key not in self._krylov:
@@ -111,11 +125,12 @@ class HelmholtzDDM:
         return self._krylov[key]
 
     def solve(self, b, restart: int = 50, rtol: float = 1e-8, max_iters: int = 1000, x0=None, out=None,
-              arnoldi: str = "auto", graphs: bool = False, reorth: str = "selective"):
+              arnoldi: str = "auto", graphs: bool = False, reorth: str = "selective", precond_steps: int = 1):
         """FGMRES solve of A x = b.  ``arnoldi``: "fp64", "ds" (double-single
         Gram-Schmidt on the FP32 pipes) or "auto" (ds with FP32 factors, fp64 with c128).
         ``reorth``: "always" (CGS2) or "selective" (second pass only after a cancellation
-        of more than a factor 10)."""
+        of more than a factor 10).  ``precond_steps``: steps of the overlapping DDM used as
+        the preconditioner (1: the one-step preconditioner of Eq. (pc))."""
         b, nrhs = self._vec(b)
         if out is not None:
             x = out
@@ -127,7 +142,8 @@ class HelmholtzDDM:
         rc, stats = B.hd_gmres_solve(self.ctx, b.data_ptr(), x.data_ptr(), nrhs, restart, max_iters, rtol,
                                      kws.data_ptr(), kws.numel(), self.scratch.data_ptr(), self.scratch_bytes,
                                      self._st(), use_x0=int(x0 is not None), arnoldi=self._arnoldi(arnoldi),
-                                     graphs=int(graphs), reorth={"always": 0, "selective": 1}[reorth])
+                                     graphs=int(graphs), reorth={"always": 0, "selective": 1}[reorth],
+                                     precond_steps=int(precond_steps))
         return x, stats
 
     def _arnoldi(self, mode: str) -> int:
