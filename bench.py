@@ -64,6 +64,9 @@ def parse():
     p.add_argument("--reorth", default="selective", choices=("always", "selective"),
                    help="second Gram-Schmidt pass always (CGS2) or only after a cancellation")
     p.add_argument("--no-autotune", dest="autotune", action="store_false")
+    p.add_argument("--study", default=None,
+                   help="overlap/PML study: comma-separated overlap:npml pairs (e.g. 0:16,8:16,24:16,8:30); one "
+                        "JSON line per pair with iterations and time per solve, then a summary line")
     p.add_argument("--precond-steps", type=int, default=1,
                    help="steps of the overlapping DDM used as the preconditioner (Eq. (ddms); 1: Eq. (pc))")
     p.add_argument("--storage", default="auto", choices=("auto", "sym", "full", "tc"),
@@ -639,6 +642,30 @@ def run_reference(args, world, rank):
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_study(args, world, rank, local):
+    """Overlap / PML-width study (the paper's N_OL comparison, Sec. 3.2): the same
+    workload solved for each (extra overlap, PML cells) pair; iterations, time per
+    solve and its split.  Prints one line per pair; returns the summary."""
+    import copy
+    rows = []
+    for pair in args.study.split(","):
+        ov, npml = (int(v) for v in pair.split(":"))
+        a = copy.copy(args)
+        a.overlap, a.npml, a.study = ov, npml, None
+        a.fp64_steps, a.e2e_steps, a.no_cpu_baseline, a.single_sample = 0, 0, True, 0
+        out = run_ours(a, world, rank, local)
+        if rank == 0:
+            row = {"overlap": ov, "npml": npml, "iters": out["iters"], "ms_per_solve": out["ms_per_step"],
+                   "breakdown_ms": out["breakdown_ms_per_step"], "relres_true": out["relres_true"]}
+            print(json.dumps({"study_point": row}), flush=True)
+            rows.append(row)
+    if rank != 0:
+        return None
+    best = min(rows, key=lambda r: r["ms_per_solve"])
+    return {"study": "overlap/npml", "config": args.config, "points": len(rows),
+            "fastest": {"overlap": best["overlap"], "npml": best["npml"], "ms_per_solve": best["ms_per_solve"]}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -649,7 +676,9 @@ def main():
             print(json.dumps(out), flush=True)
         return
     world, rank, local = dist_setup(args)
-    if args.config == "serving":
+    if args.study:
+        out = run_study(args, world, rank, local)
+    elif args.config == "serving":
         out = run_serving(args, world, rank, local)
     else:
         out = run_ours(args, world, rank, local)
