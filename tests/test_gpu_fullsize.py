@@ -94,7 +94,7 @@ def test_precond_batching_tensor_cores_sampled_boxes():
 
 
 def test_solve_4096_residual_from_oracle_operator():
-    """The headline solve (4096^2, c64 symmetric storage, double-single FGMRES(60),
+    """The headline solve (4096^2, c64 symmetric storage, double-single FGMRES(10),
     selective reorthogonalisation, rtol 1e-6): the relative residual of the GPU
     solution, formed in FP64 on the CPU with the oracle's operator, meets the
     tolerance, and the solver's own FP64 residual agrees with it."""
