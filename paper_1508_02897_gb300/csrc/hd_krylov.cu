@@ -275,6 +275,79 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, i
   }
 }
 
+// The same dot products for few basis vectors (nk + self <= KM): every warp takes a
+// DFC/8-element slice of the block's elements for all vectors (instead of one vector
+// for all elements), so short Arnoldi cycles keep every warp loading; the eight
+// warps' double-single sums are combined in a fixed order.
+template <int KM>
+__global__ void __launch_bounds__(256) k_dots_df_few(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk0,
+                                                     const double2 *__restrict__ w_all, int64_t ldw, int64_t n,
+                                                     double2 *__restrict__ partial_all, int G, int64_t ldp,
+                                                     const int *__restrict__ skip, int self) {
+  __shared__ float4 red[8][KM];
+  if (skip && skip[blockIdx.y]) return;
+  const int nk = nk0 + self;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * DFC;
+  const int cnt = (int)min((int64_t)DFC, n - base);
+  const double2 *w = w_all + (int64_t)blockIdx.y * ldw;
+  const float4 *Vr = V + (int64_t)blockIdx.y * ldvr;
+  double2 *partial = partial_all + (int64_t)blockIdx.y * ldp;
+  constexpr int U = DFC / 256;   // elements per lane
+  float4 wv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int i = warp * (DFC / 8) + u * 32 + lane;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < cnt) {
+      const double2 x = w[base + i];
+      const float2 r = split_d(x.x), m = split_d(x.y);
+      v = make_float4(r.x, r.y, m.x, m.y);
+    }
+    wv[u] = v;
+  }
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
+    if (k >= nk) break;
+    const float4 *vk = Vr + (int64_t)k * ldv + base;
+    float4 vv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = warp * (DFC / 8) + u * 32 + lane;
+      vv[u] = i < cnt ? (k < nk0 ? vk[i] : wv[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const float4 a = vv[u], b = wv[u];
+      ds_mac(rh, rl, a.x, a.y, b.x, b.y);     // re += ar br
+      ds_mac(rh, rl, a.z, a.w, b.z, b.w);     // re += ai bi
+      ds_mac(ih, il, a.x, a.y, b.z, b.w);     // im += ar bi
+      ds_mac(ih, il, -a.z, -a.w, b.x, b.y);   // im -= ai br
+    }
+    ds_renorm(rh, rl);
+    ds_renorm(ih, il);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float a = __shfl_xor_sync(0xffffffffu, rh, o), b = __shfl_xor_sync(0xffffffffu, rl, o);
+      const float c = __shfl_xor_sync(0xffffffffu, ih, o), d = __shfl_xor_sync(0xffffffffu, il, o);
+      ds_add(rh, rl, a, b);
+      ds_add(ih, il, c, d);
+    }
+    if (lane == 0) red[warp][k] = make_float4(rh, rl, ih, il);
+  }
+  __syncthreads();
+  if (tid < nk) {
+    float4 t = red[0][tid];
+    for (int q = 1; q < 8; ++q) {
+      const float4 o = red[q][tid];
+      ds_add(t.x, t.y, o.x, o.y);
+      ds_add(t.z, t.w, o.z, o.w);
+    }
+    partial[(int64_t)tid * G + blockIdx.x] = make_double2((double)t.x + (double)t.y, (double)t.z + (double)t.w);
+  }
+}
+
 // y_r = base_r - sum_k V_r[k] coef_r[k] (double-single accumulation, FP64 result);
 // optionally normpart[r][blk] = block sum of |y_r|^2.
 template <bool NORM>
@@ -352,18 +425,31 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
 }
 
 // v_r = w_r * red[4 r + 1].x written twice: split into V (double-single) and FP64 into vin.
+// SCE elements per thread with all loads issued first (one element per thread left too
+// few bytes in flight: 2.6 TB/s at 4096^2).
+constexpr int SCE = 4;
 __global__ void __launch_bounds__(256) k_scale_df(const double2 *__restrict__ w_all, int64_t ldw,
                                                   const double2 *__restrict__ red, float4 *__restrict__ vout_all,
                                                   int64_t ldvr, double2 *__restrict__ vin_all, int64_t n) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
   const int r = blockIdx.y;
+  const int64_t i0 = (int64_t)blockIdx.x * (256 * SCE) + threadIdx.x;
   const double inv = red[4 * r + 1].x;
-  double2 a = w_all[(int64_t)r * ldw + i];
-  double2 v = make_double2(a.x * inv, a.y * inv);
-  float2 cr = split_d(v.x), ci = split_d(v.y);
-  vout_all[(int64_t)r * ldvr + i] = make_float4(cr.x, cr.y, ci.x, ci.y);
-  vin_all[(int64_t)r * n + i] = v;
+  const double2 *w = w_all + (int64_t)r * ldw;
+  double2 a[SCE];
+#pragma unroll
+  for (int u = 0; u < SCE; ++u) {
+    const int64_t i = i0 + 256 * u;
+    a[u] = i < n ? w[i] : make_double2(0.0, 0.0);
+  }
+#pragma unroll
+  for (int u = 0; u < SCE; ++u) {
+    const int64_t i = i0 + 256 * u;
+    if (i >= n) break;
+    const double2 v = make_double2(a[u].x * inv, a[u].y * inv);
+    const float2 cr = split_d(v.x), ci = split_d(v.y);
+    vout_all[(int64_t)r * ldvr + i] = make_float4(cr.x, cr.y, ci.x, ci.y);
+    vin_all[(int64_t)r * n + i] = v;
+  }
 }
 
 // ---------------------------------------------------------------- small per-RHS work
@@ -568,8 +654,16 @@ struct Krylov {
   }
   cudaError_t dots_df(int nk, const double2 *x, double2 *out, int ldo, const int *skip = nullptr, int self = 0) {
     tic(ctx, T_ARNOLDI, st);
-    k_dots_df<<<dim3(L.Gdf, B), 256, sizeof(float4) * DFC, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf,
-                                                                ldp(), skip, self);
+    const dim3 grid(L.Gdf, B);
+    if (nk + self <= 4)
+      k_dots_df_few<4><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, self);
+    else if (nk + self <= 8)
+      k_dots_df_few<8><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, self);
+    else if (nk + self <= 12)
+      k_dots_df_few<12><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, self);
+    else
+      k_dots_df<<<grid, 256, sizeof(float4) * DFC, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip,
+                                                         self);
     k_reduce<<<dim3(nk + self, B), 256, 0, st>>>(part(), L.Gdf, ldp(), out, ldo, skip, 1);
     toc(ctx, T_ARNOLDI, st, 2);
     return cudaGetLastError();
@@ -634,6 +728,7 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
   const bool dsm = o->arnoldi == HD_ARNOLDI_DS;
   if (dsm) KCHK(cudaFuncSetAttribute(k_dots_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float4) * DFC)));
   const dim3 gs((unsigned)((n + 255) / 256), B);
+  const dim3 gsc((unsigned)((n + 256 * SCE - 1) / (256 * SCE)), B);
   const unsigned tb = (unsigned)std::min(B, 256), nb = (unsigned)((B + 255) / 256);
 
   // host mirror: stat [B][4] doubles | red [B][4] complex | live [B] | kcnt [B]
@@ -692,7 +787,7 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
     if ((rc = push_masks())) return rc;
     tic(ctx, T_ARNOLDI, st);
     k_cycle_init<<<nb, tb, 0, st>>>(d);
-    if (dsm) k_scale_df<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.Vdf(), K.ldvr(), K.vin(), n);
+    if (dsm) k_scale_df<<<gsc, 256, 0, st>>>(K.w(), n, d.red, K.Vdf(), K.ldvr(), K.vin(), n);
     else k_scale<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.V(), K.ldvr(), n);
     toc(ctx, T_ARNOLDI, st, 2);
     // One Arnoldi step for every live right-hand side: z_j = M v_j, w = A z_j, CGS2,
@@ -728,7 +823,7 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
       if (sel) ctx->t_launch[T_ARNOLDI] += 1;
       tic(ctx, T_ARNOLDI, st);
       k_arnoldi_step<<<nb, tb, 0, st>>>(d, j);
-      if (dsm) k_scale_df<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.Vdf() + (int64_t)(j + 1) * n, K.ldvr(), K.vin(), n);
+      if (dsm) k_scale_df<<<gsc, 256, 0, st>>>(K.w(), n, d.red, K.Vdf() + (int64_t)(j + 1) * n, K.ldvr(), K.vin(), n);
       else k_scale<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.V() + (int64_t)(j + 1) * n, K.ldvr(), n);
       toc(ctx, T_ARNOLDI, st, 2);
       KCHK(cudaGetLastError());

@@ -662,8 +662,9 @@ static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, dou
   if (ctx->tc || ctx->sym) {
     tic(ctx, T_SUBST, st);
     cudaError_t e = ctx->tc ? launch_subst_tc(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
-                    : ctx->max_m <= 192 ? launch_subst_sym_nr<R, S, 6>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
-                                        : launch_subst_sym_nr<R, S, 8>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st);
+                    : (ctx->max_m <= 192 && ctx->tune_ct != 256)
+                        ? launch_subst_sym_nr<R, S, 6>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
+                        : launch_subst_sym_nr<R, S, 8>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st);
     toc(ctx, T_SUBST, st, 1);
     if (e != cudaSuccess) return e;
     dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
@@ -778,11 +779,13 @@ int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cud
   // one ring stage: NW warps x tiles per warp (symmetric) or chunk_cols<S>() columns of
   // ldmax entries (64 bytes per row)
   const size_t sb = store_bytes(ctx->prec);
-  const size_t stage = ctx->sym ? (size_t)(ctx->max_m <= 192 ? 6 : 8) * (sb == 4 ? 2 : 1) * TB * TB * sb
-                                : (size_t)ldmax * 64;
+  // symmetric storage: 6 or 8 consumer warps (192 or 256 threads) x tiles per warp per stage
+  auto stage_of = [&](int ct) {
+    return ctx->sym ? (size_t)(ct / 32) * (sb == 4 ? 2 : 1) * TB * TB * sb : (size_t)ldmax * 64;
+  };
   int dev_optin = 0;
   cudaDeviceGetAttribute(&dev_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  std::vector<int> cts = ctx->sym ? std::vector<int>{ctx->max_m <= 192 ? 192 : 256}
+  std::vector<int> cts = ctx->sym ? (ctx->max_m <= 192 ? std::vector<int>{192, 256} : std::vector<int>{256})
                                   : (ctx->max_m <= 192 ? std::vector<int>{96, 128, 192} : std::vector<int>{128, 256});
   const int ns_list[] = {2, 3, 4, 6, 8, 12, 16, 24, 32};
   cudaEvent_t e0, e1;
@@ -794,7 +797,7 @@ int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cud
   ctx->profiling = false;
   for (int ct : cts)
     for (int ns : ns_list) {
-      if ((size_t)ns * stage + (ctx->sym ? 24576 : 8192) > (size_t)std::min(dev_optin, 224 * 1024)) continue;
+      if ((size_t)ns * stage_of(ct) + (ctx->sym ? 24576 : 8192) > (size_t)std::min(dev_optin, 224 * 1024)) continue;
       ctx->tune_ct = ct;
       ctx->tune_ns = ns;
       float tot = 0.f;
