@@ -116,6 +116,13 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
+// d_entry restricted to its tridiagonal band (zero elsewhere without touching the tables)
+template <typename T, typename R>
+__device__ __forceinline__ T d_band(int r, int c, int j, const double2 *a1c, const double2 *ia1f, const double2 *a2c,
+                                    const double2 *ia2f, const double *k2row, double h2) {
+  return (r - c <= 1 && c - r <= 1) ? d_entry<T, R>(r, c, j, a1c, ia1f, a2c, ia2f, k2row, h2) : mk<T>(0, 0);
+}
+
 template <typename R, typename S, int LAY>
 __global__ void __launch_bounds__(FT, factor_ctas<R>())
 k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const double *__restrict__ k2, int NX,
@@ -167,16 +174,36 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
       __syncthreads();
       const S *prev = Fs + (int64_t)(j - 1) * slot_elems;
       const double *k2row = k2 + (int64_t)(s.ey0 + j) * NX + s.ex0;
-      for (int64_t idx = tid; idx < mm; idx += FT) {
-        const int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
-        T v;
-        if (SYM) {
-          const int a = min(r, c), b = max(r, c), I = a >> 4, J = b >> 4, rr = a & 15, cc = b & 15;
-          v = load_c<T>(prev[(int64_t)(J * (J + 1) / 2 + I) * 256 + cc * 16 + ((rr + cc) & 15)]);
-        } else {
-          v = load_c<T>(prev[(int64_t)c * ldm + r]);
+      if (SYM) {
+        // tile by tile: stored tile (I, J), I <= J, is block (I, J) of S_{j-1}^{-1} and, off the
+        // diagonal, the transpose of block (J, I); one FT-thread pass per tile and block,
+        // consecutive threads on consecutive rows of W (and of the tile's storage)
+        static_assert(FT == 256, "one thread per tile entry");
+        const int mt = (m + 15) / 16;
+        for (int J = 0, u = 0; J < mt; ++J)
+          for (int I = 0; I <= J; ++I, ++u) {
+            const S *tile = prev + (int64_t)u * 256;
+            {
+              const int cc = tid >> 4, rr = ((tid & 15) - cc) & 15;   // storage order
+              const int r = 16 * I + rr, c = 16 * J + cc;
+              if (r < m && c < m)
+                W[(int64_t)c * m + r] = cfms(cmul(lS[r], load_c<T>(tile[tid])), lS[c],
+                                             d_band<T, R>(r, c, j, a1c, ia1f, a2c, ia2f, k2row, h2));
+            }
+            if (I < J) {
+              const int rr = tid >> 4, cc = tid & 15;   // W(16J + cc, 16I + rr) = S(16I + rr, 16J + cc)
+              const int r = 16 * J + cc, c = 16 * I + rr;
+              if (r < m && c < m)
+                W[(int64_t)c * m + r] = cfms(cmul(lS[r], load_c<T>(tile[cc * 16 + ((rr + cc) & 15)])), lS[c],
+                                             d_band<T, R>(r, c, j, a1c, ia1f, a2c, ia2f, k2row, h2));
+            }
+          }
+      } else {
+        for (int64_t idx = tid; idx < mm; idx += FT) {
+          const int c = (int)(idx / m), r = (int)(idx - (int64_t)c * m);
+          W[idx] = cfms(cmul(lS[r], load_c<T>(prev[(int64_t)c * ldm + r])), lS[c],
+                        d_band<T, R>(r, c, j, a1c, ia1f, a2c, ia2f, k2row, h2));
         }
-        W[idx] = cfms(cmul(lS[r], v), lS[c], d_entry<T, R>(r, c, j, a1c, ia1f, a2c, ia2f, k2row, h2));
       }
       __syncthreads();
     }
@@ -349,14 +376,14 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
             const int cc = idx / m, r = idx - cc * m, c = c0 + cc;
             if (r <= c)
               W2[(int64_t)c * m + r] =
-                  cfms(cmul(lS[r], Q[cc * m + r]), lS[c], d_entry<T, R>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
+                  cfms(cmul(lS[r], Q[cc * m + r]), lS[c], d_band<T, R>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
           }
           // ... and their mirror images (c, r) below the diagonal
           for (int idx = tid; idx < 16 * m; idx += FT) {
             const int cc = idx & 15, r = idx >> 4, c = c0 + cc;
             if (cc < nc && r < c)
               W2[(int64_t)r * m + c] =
-                  cfms(cmul(lS[c], Q[cc * m + r]), lS[r], d_entry<T, R>(c, r, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
+                  cfms(cmul(lS[c], Q[cc * m + r]), lS[r], d_band<T, R>(c, r, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
           }
         }
       } else {
@@ -364,7 +391,7 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
           const int cc = idx / m, r = idx - cc * m, c = c0 + cc;
           const T v = Q[cc * m + r];
           if (!TCL) slot[(int64_t)c * ldm + r] = store_c<S>(v);
-          if (more) W2[(int64_t)c * m + r] = cfms(cmul(lS[r], v), lS[c], d_entry<T, R>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
+          if (more) W2[(int64_t)c * m + r] = cfms(cmul(lS[r], v), lS[c], d_band<T, R>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
         }
         if (TCL) {
           // chunks 2J, 2J+1 (8 columns each) of the block, each the real then the imaginary
