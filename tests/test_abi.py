@@ -29,3 +29,25 @@ def test_invalid_arguments_are_rejected_without_gpu():
     rc = B.lib().hd_setup_medium(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(d), None, 0, None)
     assert rc == B.HD_ERR_INVALID and not ctx.value
     assert "NULL" in B.hd_last_error() or "bad" in B.hd_last_error()
+
+
+def test_storage_flags_and_new_entry_points_validate_without_gpu():
+    """Host-side checks run before any CUDA call: the tensor-core storage flag is
+    refused with FP64 factors or together with symmetric storage, an unknown flag
+    bit is refused, and the multi-step DDM and FGMRES entry points refuse NULL
+    contexts, zero steps and bad options."""
+    from paper_1508_02897_gb300 import _binding as B
+    L = B.lib()
+    g = B.hd_grid(64, 64, 8, 1.0 / 64, 40.0, 20.0, 2)
+    d = B.hd_decomp(2, 2, 4, None, None, 1)
+    fake_c = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+    for prec in (B.HD_C128 | B.HD_TCORE, B.HD_C64 | B.HD_TCORE | B.HD_SYMMETRIC, B.HD_C64 | 0x400, 7):
+        ctx = ctypes.c_void_p()
+        rc = L.hd_setup_medium(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(d), fake_c, prec, None)
+        assert rc == B.HD_ERR_INVALID and not ctx.value, prec
+    assert "precision" in B.hd_last_error() or "HD_TCORE" in B.hd_last_error()
+    p = ctypes.c_void_p(16)
+    assert L.hd_apply_ddm(None, p, p, 1, 2, p, 1 << 20, p, 1 << 20, None) == B.HD_ERR_INVALID
+    o = B.hd_gmres_opts(10, 100, 1e-6, 0, B.HD_ARNOLDI_DS, 0, 1, 1)
+    st = (B.hd_gmres_stats * 1)()
+    assert L.hd_gmres_solve(None, p, p, 1, ctypes.byref(o), p, 1 << 20, p, 1 << 20, st, None) == B.HD_ERR_INVALID
