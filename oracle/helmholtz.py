@@ -40,7 +40,8 @@ import scipy.sparse.linalg as spla
 
 __all__ = [
     "Grid", "Subdomain", "pml_profile", "helmholtz_matrix", "global_operator", "rhs_from_source",
-    "decompose", "local_operator", "DDMPreconditioner", "fgmres", "FGMRESResult",
+    "decompose", "local_operator", "DDMPreconditioner", "fgmres", "FGMRESResult", "smoothstep5",
+    "smoothing_profile",
 ]
 
 
@@ -187,6 +188,28 @@ def local_operator(grid: Grid, k2: np.ndarray, s: Subdomain) -> sp.csr_matrix:
     return helmholtz_matrix(k2[s.ey0:s.ey1, s.ex0:s.ex1], ax_c, ax_f, ay_c, ay_f, grid.h)
 
 
+def smoothstep5(t: np.ndarray) -> np.ndarray:
+    """t^3 (10 - 15 t + 6 t^2): 0 at t = 0, 1 at t = 1, first and second derivatives
+    zero at both ends (a C^2 step)."""
+    t = np.clip(np.asarray(t, dtype=np.float64), 0.0, 1.0)
+    return t * t * t * (10.0 - 15.0 * t + 6.0 * t * t)
+
+
+def smoothing_profile(o0: int, o1: int, e0: int, e1: int) -> np.ndarray:
+    """One axis of the smoothing function beta_ij of the Remark after Eq. (pc) over the
+    cells [e0, e1) of a box: 1 on the owned cells [o0, o1), falling to 0 across the band
+    between the owned part and the edge of the box (reading: beta is the tensor product
+    of C^2 steps of the cell distance d from the owned part, beta = S(1 - d / (W + 1))
+    with W the band width, so it reaches 0 just outside the box)."""
+    x = np.arange(e0, e1)
+    b = np.ones(e1 - e0)
+    lo = x < o0
+    b[lo] = smoothstep5(1.0 - (o0 - x[lo]) / (o0 - e0 + 1.0))
+    hi = x >= o1
+    b[hi] = smoothstep5(1.0 - (x[hi] - o1 + 1) / (e1 - o1 + 1.0))
+    return b
+
+
 class DDMPreconditioner:
     """One-step preconditioner of Eq. (ddm0) and Eq. (pc): restrict the input to
     every owned box, solve every local PML problem, and add each full local
@@ -196,8 +219,9 @@ class DDMPreconditioner:
     solver"; the paper does not name it)."""
 
     def __init__(self, grid: Grid, c: np.ndarray, cut_x, cut_y, overlap: int,
-                 own_global_pml: bool = True, subdomains: Optional[Sequence[int]] = None):
+                 own_global_pml: bool = True, subdomains: Optional[Sequence[int]] = None, smoothing: bool = False):
         self.grid = grid
+        self.smoothing = smoothing
         self.c = np.asarray(c, dtype=np.float64)
         self.k2 = (grid.omega / self.c) ** 2
         self._A = None
@@ -215,13 +239,20 @@ class DDMPreconditioner:
         rho[s.oy0 - s.ey0:s.oy1 - s.ey0, s.ox0 - s.ex0:s.ox1 - s.ex0] = r[s.oy0:s.oy1, s.ox0:s.ox1]
         return self.lu[s_idx].solve(rho.ravel()).reshape(rho.shape)
 
+    def beta(self, s_idx: int) -> np.ndarray:
+        """beta_ij over the box (rows y, columns x), Remark after Eq. (pc)."""
+        s = self.subs[s_idx]
+        return np.outer(smoothing_profile(s.oy0, s.oy1, s.ey0, s.ey1), smoothing_profile(s.ox0, s.ox1, s.ex0, s.ex1))
+
     def apply(self, r: np.ndarray) -> np.ndarray:
-        """u_PC = sum_ij u_ij^0 over each full box Omega_ij, Eq. (pc)."""
+        """u_PC = sum_ij u_ij^0 over each full box Omega_ij, Eq. (pc); with smoothing,
+        sum_ij beta_ij u_ij^0 (the Remark after Eq. (pc))."""
         r = np.asarray(r, dtype=np.complex128).reshape(self.grid.n, self.grid.n)
         z = np.zeros_like(r)
         for s_idx in self.active:
             s = self.subs[s_idx]
-            z[s.ey0:s.ey1, s.ex0:s.ex1] += self.local_solve(s_idx, r)
+            u = self.local_solve(s_idx, r)
+            z[s.ey0:s.ey1, s.ex0:s.ex1] += self.beta(s_idx) * u if self.smoothing else u
         return z
 
     def neighbours(self, s_idx: int) -> List[int]:
@@ -242,6 +273,8 @@ class DDMPreconditioner:
         """
         if steps < 1:
             raise ValueError("steps must be >= 1")
+        if self.smoothing:
+            raise ValueError("the multi-step form is built without the smoothing function")
         g = self.grid
         if self._A is None:
             self._A = global_operator(g, self.c)

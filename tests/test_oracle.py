@@ -212,6 +212,68 @@ def test_dense_brute_force_preconditioner():
     np.testing.assert_allclose(P.apply(r).ravel(), M @ r, rtol=1e-11, atol=1e-12)
 
 
+# ---------------------------------------------------------------- smoothing function (Remark after Eq. (pc))
+def test_smoothstep_is_a_c2_step():
+    """S(0) = 0, S(1) = 1 and S', S'' vanish at both ends (C^2 step), from the
+    closed-form derivatives 30 t^2 (1 - t)^2 and 60 t (1 - t)(1 - 2 t)."""
+    from oracle import smoothstep5
+    t = np.linspace(0.0, 1.0, 2001)
+    S = smoothstep5(t)
+    assert S[0] == 0.0 and S[-1] == 1.0 and np.all(np.diff(S) >= 0)
+    h = t[1] - t[0]
+    d1 = np.gradient(S, h)
+    d2 = np.gradient(d1, h)
+    np.testing.assert_allclose(d1, 30 * t**2 * (1 - t)**2, atol=1e-4)
+    np.testing.assert_allclose(d2[2:-2], (60 * t * (1 - t) * (1 - 2 * t))[2:-2], atol=1e-3)
+
+
+def test_smoothing_profile_one_on_owned_zero_past_the_box():
+    """beta = 1 on the owned cells, strictly between 0 and 1 in the band, and its
+    continuation is 0 one cell past the box (the Remark: beta = 1 on the owned part,
+    0 outside Omega_ij)."""
+    from oracle import smoothing_profile, smoothstep5
+    o0, o1, e0, e1 = 24, 88, 12, 100
+    b = smoothing_profile(o0, o1, e0, e1)
+    assert np.all(b[o0 - e0:o1 - e0] == 1.0)
+    band = np.r_[b[:o0 - e0], b[o1 - e0:]]
+    assert np.all((band > 0) & (band < 1))
+    assert smoothstep5(1.0 - (o0 - (e0 - 1)) / (o0 - e0 + 1.0)) == 0.0
+    assert np.all(np.diff(b[:o0 - e0 + 1]) > 0) and np.all(np.diff(b[o1 - e0 - 1:]) < 0)
+
+
+def test_smoothed_preconditioner_dense_brute_force():
+    """sum_ij E_ij^T diag(beta_ij) inv(A_ij) X_ij formed densely on 12^2 with 2x2 boxes
+    equals the smoothed application; with one box beta is 1 on the whole box and
+    the smoothed preconditioner is still the exact inverse."""
+    N, npml = 12, 4
+    g = Grid(N=N, npml=npml, omega=8.0)
+    c = W.velocity_random_field(N, npml, seed=9)
+    cuts = W.even_cuts(N, npml, 2)
+    P = DDMPreconditioner(g, c, cuts, cuts, overlap=1, smoothing=True)
+    n2 = g.n * g.n
+    M = np.zeros((n2, n2), complex)
+    for b, s in enumerate(P.subs):
+        ex, ey = s.ex1 - s.ex0, s.ey1 - s.ey0
+        E = np.zeros((ex * ey, n2))
+        X = np.zeros((ex * ey, n2))
+        for ly in range(ey):
+            for lx in range(ex):
+                gi = (s.ey0 + ly) * g.n + s.ex0 + lx
+                E[ly * ex + lx, gi] = 1.0
+                if s.ox0 <= s.ex0 + lx < s.ox1 and s.oy0 <= s.ey0 + ly < s.oy1:
+                    X[ly * ex + lx, gi] = 1.0
+        Ainv = np.linalg.inv(local_operator(g, P.k2, s).toarray())
+        M += E.T @ np.diag(P.beta(b).ravel()) @ Ainv @ X
+    r = W.random_complex(n2, seed=4)
+    np.testing.assert_allclose(P.apply(r).ravel(), M @ r, rtol=1e-11, atol=1e-12)
+    assert not np.allclose(P.apply(r), DDMPreconditioner(g, c, cuts, cuts, overlap=1).apply(r))
+    wl = W.make_workload("tiny", N=48, nb=1)
+    g1 = Grid(wl.N, wl.npml, wl.omega)
+    P1 = DDMPreconditioner(g1, wl.c, wl.cut_x, wl.cut_y, wl.overlap, smoothing=True)
+    r1 = W.random_complex(g1.n * g1.n, seed=11)
+    np.testing.assert_allclose(P1.apply(r1).ravel(), _solve(global_operator(g1, wl.c), r1), rtol=1e-12, atol=1e-12)
+
+
 # ---------------------------------------------------------------- multi-step DDM
 def _ddm_case():
     wl = W.make_workload("tiny", N=96, nb=3, medium="three_layer")
