@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--study", default=None,
                    help="overlap/PML study: comma-separated overlap:npml pairs (e.g. 0:16,8:16,24:16,8:30); one "
                         "JSON line per pair with iterations and time per solve, then a summary line")
+    p.add_argument("--smoothing", action="store_true",
+                   help="weight each local solution by the smoothing function beta (Remark after Eq. (pc))")
     p.add_argument("--precond-steps", type=int, default=1,
                    help="steps of the overlapping DDM used as the preconditioner (Eq. (ddms); 1: Eq. (pc))")
     p.add_argument("--storage", default="auto", choices=("auto", "sym", "full", "tc"),
@@ -266,7 +268,8 @@ def run_ours(args, world, rank, local):
         storage = storage or args.storage
         s = HelmholtzDDM(wl.N, wl.npml, wl.omega, c_d, wl.nbx, wl.nby, wl.overlap, precision=precision,
                          cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev),
-                         symmetric=storage == "sym", tcore=storage == "tc" and precision == "c64")
+                         symmetric=storage == "sym", tcore=storage == "tc" and precision == "c64",
+                         smoothing=args.smoothing)
         s.set_profiling(profile)
         s.factor()
         if args.autotune:
@@ -357,7 +360,7 @@ def run_ours(args, world, rank, local):
                    "overlap": wl.overlap, "restart": wl.restart, "rtol": wl.rtol, "precision": args.precision,
                    "omega": wl.omega, "l2": "inputs larger than L2 (factors %.1f GB, Krylov basis %.1f GB)" % (
                        _factor_gb(wl, fs, sym), 2 * (wl.restart + 1) * n_unk * 16 / 1e9),
-                   "precond_steps": args.precond_steps,
+                   "precond_steps": args.precond_steps, "smoothing": bool(args.smoothing),
                    "factor_storage": {"sym": "upper 16x16 tiles (symmetric)", "full": "full blocks",
                                       "tc": "TF32 real/imag planes, tensor-core operand layout"}[sym],
                    "parallelism": f"replicas x{world} (one independent solve per GPU)"},

@@ -71,6 +71,14 @@ typedef enum {
  * entry.  The factorisation itself stays FP32; only the stored copy is TF32. */
 #define HD_TCORE 0x200
 
+/* Flag OR-ed into any precision: weight every local solution by the smoothing
+ * function beta_ij of the Remark after Eq. (pc) before the sum of Eq. (pc)
+ * (beta = 1 on the owned cells, a C^2 step t^3 (10 - 15 t + 6 t^2) of the distance
+ * across the overlap + PML band, 0 just past the box; the paper states the
+ * properties, not the profile).  Applies to the one-step preconditioner, and
+ * hd_apply_ddm then does residual correction with this smoothed M. */
+#define HD_SMOOTH 0x400
+
 /* Truncated domain Omega of Sec. 2: interior nx x ny cells of width h (the
  * interior is [0, nx h] x [0, ny h]), npml PML cells per side.  The PML uses
  * alpha(xi) = 1 + i sigma(xi)/omega with sigma(xi)/omega =

@@ -152,7 +152,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
     return invalid("hd_setup_medium: bad decomposition");
   const int base_prec = precision & 0xff;
   if ((base_prec != HD_C128 && base_prec != HD_C64 && base_prec != HD_C64_H) ||
-      (precision & ~(0xff | HD_SYMMETRIC | HD_TCORE)))
+      (precision & ~(0xff | HD_SYMMETRIC | HD_TCORE | HD_SMOOTH)))
     return invalid("hd_setup_medium: bad precision");
   if ((precision & HD_TCORE) && (base_prec != HD_C64 || (precision & HD_SYMMETRIC)))
     return invalid("hd_setup_medium: HD_TCORE needs HD_C64 and excludes HD_SYMMETRIC");
@@ -165,6 +165,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   c->prec = base_prec;
   c->sym = (precision & HD_SYMMETRIC) != 0;
   c->tc = (precision & HD_TCORE) != 0;
+  c->smooth = (precision & HD_SMOOTH) != 0;
   c->stream = st;
   c->nbx = dec->nbx; c->nby = dec->nby; c->overlap = dec->overlap; c->own_global_pml = dec->own_global_pml ? 1 : 0;
   std::vector<int32_t> nearx, neary;

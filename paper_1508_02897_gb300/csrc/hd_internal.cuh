@@ -125,6 +125,7 @@ struct hd_ctx {
   int prec;
   bool sym = false;   // S_j^{-1} stored as upper 16 x 16 tiles (HD_SYMMETRIC)
   bool tc = false;    // S_j^{-1} stored in the tensor-core operand layout (HD_TCORE)
+  bool smooth = false;   // local solutions weighted by the smoothing function beta (HD_SMOOTH)
   // decomposition
   int nbx, nby, overlap, own_global_pml;
   int nsub;

@@ -528,6 +528,16 @@ k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, c
   }
 }
 
+// One axis of the smoothing function beta_ij (Remark after Eq. (pc)) at cell x of a box
+// [e0, e1) owning [o0, o1): 1 on the owned cells, else the C^2 step
+// S(t) = t^3 (10 - 15 t + 6 t^2) of t = 1 - d / (W + 1), d the distance from the owned
+// cells and W the width of the band on that side (so beta reaches 0 just past the box).
+template <typename R> __device__ __forceinline__ R smooth_beta(int x, const AxisDev &a) {
+  if (x >= a.o0 && x < a.o1) return (R)1;
+  const R t = x < a.o0 ? (R)1 - (R)(a.o0 - x) / (R)(a.o0 - a.e0 + 1) : (R)1 - (R)(x - a.o1 + 1) / (R)(a.e1 - a.o1 + 1);
+  return t * t * t * ((R)10 - (R)15 * t + (R)6 * t * t);
+}
+
 // The sum runs in the compute precision of the local solutions (FP32 for the c64
 // modes: one conversion per cell instead of one per contribution, since the FP64
 // pipe is the scarce one on this GPU) and is written out as complex128.
@@ -536,8 +546,9 @@ __global__ void __launch_bounds__(256)
 k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const AxisDev *__restrict__ axy,
          const int32_t *__restrict__ nearx, const int32_t *__restrict__ neary, int nbx, int nby,
          const C<R> *__restrict__ staging_all, int64_t stg_stride, double2 *__restrict__ z_all, int64_t vec_stride,
-         int NX) {
+         int NX, int smooth) {
   __shared__ int ylist[3], yoff[3], ny_s;
+  __shared__ R ybeta[3];
   const int gy = blockIdx.y;
   if (threadIdx.x == 0) {
     // boxes whose extent covers grid row gy (at most 3, in practice 1 or 2)
@@ -545,7 +556,12 @@ k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const
     int cnt = 0;
     for (int jy = max(iy - 1, 0); jy <= min(iy + 1, nby - 1); ++jy) {
       const AxisDev ay = axy[jy];
-      if (gy >= ay.e0 && gy < ay.e1) { ylist[cnt] = jy; yoff[cnt] = gy - ay.e0; ++cnt; }
+      if (gy >= ay.e0 && gy < ay.e1) {
+        ylist[cnt] = jy;
+        yoff[cnt] = gy - ay.e0;
+        ybeta[cnt] = smooth_beta<R>(gy, ay);
+        ++cnt;
+      }
     }
     ny_s = cnt;
   }
@@ -564,7 +580,12 @@ k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const
       if (gx < ax.e0 || gx >= ax.e1) continue;
       const int ex = ax.e1 - ax.e0;
       const C<R> v = staging[subs[jy * nbx + jx].soff + (int64_t)ry * ex + (gx - ax.e0)];
-      acc = cadd(acc, v);
+      if (smooth) {   // beta_ij u_ij (Remark after Eq. (pc))
+        const R b = mul_rn(ybeta[q], smooth_beta<R>(gx, ax));
+        acc = mk<C<R>>(fma_rn(b, v.x, acc.x), fma_rn(b, v.y, acc.y));
+      } else {
+        acc = cadd(acc, v);
+      }
     }
   }
   z[(int64_t)gy * NX + gx] = make_double2((double)acc.x, (double)acc.y);
@@ -671,7 +692,7 @@ static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, dou
     tic(ctx, T_GATHER, st);
     k_gather<R><<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
                                       ctx->nby, reinterpret_cast<const C<R> *>(staging), ctx->staging_elems, z, zs,
-                                      ctx->NX);
+                                      ctx->NX, ctx->smooth ? 1 : 0);
     toc(ctx, T_GATHER, st, 1);
     return cudaGetLastError();
   }
@@ -692,7 +713,7 @@ static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, dou
   tic(ctx, T_GATHER, st);
   k_gather<R><<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
                                     ctx->nby, reinterpret_cast<const C<R> *>(staging), ctx->staging_elems, z, zs,
-                                    ctx->NX);
+                                    ctx->NX, ctx->smooth ? 1 : 0);
   toc(ctx, T_GATHER, st, 1);
   return cudaGetLastError();
 }

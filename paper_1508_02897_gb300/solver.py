@@ -16,13 +16,15 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> int:
     return int(s.cuda_stream)
 
 
-def _storage_flag(prec: int, symmetric: bool, tcore: bool) -> int:
-    """Storage of the S_j^{-1}: tensor-core operand layout (c64 only), upper tiles, or full."""
+def _storage_flag(prec: int, symmetric: bool, tcore: bool, smoothing: bool = False) -> int:
+    """Storage of the S_j^{-1} (tensor-core operand layout, c64 only; upper tiles; or
+    full) and the optional smoothing function of the sum of local solutions."""
+    sm = B.HD_SMOOTH if smoothing else 0
     if tcore:
         if prec != B.HD_C64:
             raise ValueError("tensor-core storage needs precision c64")
-        return B.HD_TCORE
-    return B.HD_SYMMETRIC if symmetric else 0
+        return B.HD_TCORE | sm
+    return (B.HD_SYMMETRIC if symmetric else 0) | sm
 
 
 class HelmholtzDDM:
@@ -36,7 +38,7 @@ class HelmholtzDDM:
                  precision: str = "c64", cut_x: Optional[Sequence[int]] = None, cut_y: Optional[Sequence[int]] = None,
                  own_global_pml: bool = True, sigma0_over_omega: float = 20.0, pml_power: int = 2,
                  device: str = "cuda", stream: Optional[torch.cuda.Stream] = None, factor: bool = True,
-                 symmetric: bool = True, tcore: bool = False):
+                 symmetric: bool = True, tcore: bool = False, smoothing: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("HelmholtzDDM needs a CUDA device: there is no CPU path")
         self.N, self.npml, self.n = N, npml, N + 2 * npml
@@ -47,7 +49,7 @@ class HelmholtzDDM:
                               dtype=torch.float64).to(self.device).contiguous()
         assert c_t.shape == (self.n, self.n), f"velocity must be {(self.n, self.n)}"
         self.ctx = B.hd_setup_medium(N, N, npml, 1.0 / N, omega, c_t.data_ptr(),
-                                     self.prec | _storage_flag(self.prec, symmetric, tcore), self._st(),
+                                     self.prec | _storage_flag(self.prec, symmetric, tcore, smoothing), self._st(),
                                      nbx, nby, overlap, cut_x, cut_y, int(own_global_pml), sigma0_over_omega,
                                      pml_power)
         fb, _, sb = B.hd_query_workspace(self.ctx, 1, 1)
@@ -172,7 +174,7 @@ class HelmholtzDDM:
 def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: int, overlap: int,
                restart: int, rtol: float, max_iters: int = 5000, precision: str = "c64", cut_x=None, cut_y=None,
                device: str = "cuda", arnoldi: str = "auto", symmetric: bool = True, reorth: str = "selective",
-               tcore: bool = False):
+               tcore: bool = False, smoothing: bool = False):
     """End-to-end solve from host arrays: velocity c [n][n] (float64) and source
     samples f [nrhs][n][n] (complex128), preferably in pinned memory.  Copies in,
     sets up the medium, factorises, forms b = J h^2 f, runs FGMRES and copies the
@@ -181,7 +183,7 @@ def solve_host(c_host, f_host, N: int, npml: int, omega: float, nbx: int, nby: i
     c_d = torch.as_tensor(c_host).to(dev, non_blocking=True)
     f_d = torch.as_tensor(f_host).to(dev, non_blocking=True)
     s = HelmholtzDDM(N, npml, omega, c_d, nbx, nby, overlap, precision=precision, cut_x=cut_x, cut_y=cut_y,
-                     device=device, symmetric=symmetric, tcore=tcore)
+                     device=device, symmetric=symmetric, tcore=tcore, smoothing=smoothing)
     b = s.rhs(f_d)
     x, stats = s.solve(b, restart=restart, rtol=rtol, max_iters=max_iters, arnoldi=arnoldi, reorth=reorth)
     x_h = x.to("cpu")
@@ -199,7 +201,8 @@ class Server:
         self._keep = {}
 
     def submit(self, c, f, N, npml, omega, nbx, nby, overlap, restart, rtol, max_iters=5000, precision="c64",
-               cut_x=None, cut_y=None, arnoldi="auto", symmetric=True, reorth="selective", tcore=False):
+               cut_x=None, cut_y=None, arnoldi="auto", symmetric=True, reorth="selective", tcore=False,
+               smoothing=False):
         """c: float64 [n][n], f: complex128 [nrhs][n][n] host arrays.  Returns a ticket."""
         c = np.ascontiguousarray(c, dtype=np.float64)
         f = np.ascontiguousarray(f, dtype=np.complex128)
@@ -209,7 +212,7 @@ class Server:
         prec = {"c64": B.HD_C64, "c64h": B.HD_C64_H, "c128": B.HD_C128}[precision]
         mode = arnoldi if arnoldi != "auto" else ("ds" if prec != B.HD_C128 else "fp64")
         t = B.hd_submit(self.srv, N, N, npml, 1.0 / N, omega, c.ctypes.data, f.ctypes.data, f.shape[0],
-                        prec | _storage_flag(prec, symmetric, tcore),
+                        prec | _storage_flag(prec, symmetric, tcore, smoothing),
                         restart, max_iters, rtol, x.ctypes.data, nbx, nby, overlap, cut_x, cut_y,
                         arnoldi={"fp64": B.HD_ARNOLDI_FP64, "ds": B.HD_ARNOLDI_DS}[mode],
                         reorth={"always": 0, "selective": 1}[reorth])

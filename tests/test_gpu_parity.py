@@ -265,3 +265,52 @@ def test_gmres_multistep_preconditioner():
     x2, st2 = s.solve(torch.from_numpy(b), restart=50, rtol=1e-8, max_iters=300, precond_steps=2)
     assert st2[0]["converged"] == 1 and st2[0]["iters"] < st1[0]["iters"]
     assert np.linalg.norm(b.ravel() - A @ x2.cpu().numpy().ravel()) / np.linalg.norm(b) <= 1e-8
+
+
+# ---------------------------------------------------------------- smoothing function beta
+def _gpu_smooth(name, precision):
+    case, c, g, _, _ = oracle(name)
+    return HelmholtzDDM(case["N"], case["npml"], g.omega, c, case["nb"], case["nb"], case["overlap"],
+                        precision=precision.rstrip("st"), cut_x=cuts(case), cut_y=cuts(case),
+                        symmetric=precision.endswith("s"), tcore=precision.endswith("t"), smoothing=True)
+
+
+_smooth_oracles = {}
+
+
+def _oracle_smooth(name):
+    if name not in _smooth_oracles:
+        case, c, g, A, _ = oracle(name)
+        _smooth_oracles[name] = DDMPreconditioner(g, c, cuts(case), cuts(case), case["overlap"], smoothing=True)
+    return _smooth_oracles[name]
+
+
+@pytest.mark.parametrize("name", ["ragged", "layers4"])
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64s", 2e-4), ("c64t", 3e-2)])
+def test_precond_smoothing_parity(name, precision, tol):
+    """HD_SMOOTH: every local solution weighted by beta_ij before the sum (Remark after
+    Eq. (pc)), against the oracle's smoothed preconditioner; two sources."""
+    _, _, g, _, _ = oracle(name)
+    P = _oracle_smooth(name)
+    s = _gpu_smooth(name, precision)
+    r = W.random_complex((2, g.n, g.n), seed=19)
+    z = s.apply_precond(torch.from_numpy(r)).cpu().numpy()
+    for k in range(2):
+        assert rel(z[k], P.apply(r[k])) < tol
+
+
+def test_gmres_smoothing_fixed_steps_and_convergence():
+    """FGMRES with the smoothed preconditioner: the iterate after k steps matches the
+    oracle's FGMRES with the smoothed M (FP64 paths), and the solve converges."""
+    case, c, g, A, _ = oracle("layers4")
+    P = _oracle_smooth("layers4")
+    s = _gpu_smooth("layers4", "c128")
+    b = rhs_from_source(g, W.gaussian_source(case["N"], case["npml"], 0.45, 0.4, 2.0 / case["N"]))
+    k = 4
+    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=3, rtol=1e-15, max_iters=k)
+    x, st = s.solve(torch.from_numpy(b), restart=3, rtol=1e-15, max_iters=k, arnoldi="fp64")
+    assert st[0]["iters"] == ref.iters == k
+    assert rel(x.cpu().numpy(), ref.x.reshape(g.n, g.n)) < 1e-9
+    x2, st2 = s.solve(torch.from_numpy(b), restart=50, rtol=1e-8, max_iters=300)
+    assert st2[0]["converged"] == 1
+    assert np.linalg.norm(b.ravel() - A @ x2.cpu().numpy().ravel()) / np.linalg.norm(b) <= 1e-8
