@@ -36,7 +36,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "precond GMRES solves/s & unknown·iters/s at 4096², p50/p99 latency, vs FP64 plain path"
 HBM_FALLBACK_GBS = 6800.0      # profiling recipe fallback (no MEASURED_PEAKS.json)
-FP64_PEAK_TFLOPS = 1.195       # FP64 FMA rate measured on this machine's GB300
+FP64_PEAK_TFLOPS = 1.195       # FP64 FMA rate measured on a GB300 with hd_probe_peaks
 
 
 def parse():
