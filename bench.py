@@ -542,10 +542,12 @@ def run_serving(args, world, rank, local):
         now = time.perf_counter() - t0
         if t_arr > now:
             time.sleep(t_arr - now)
+        # storage per request: tensor cores for 8 or more sources (auto), else symmetric tiles
+        tc = args.storage == "tc" or (args.storage == "auto" and wl.nrhs >= 8 and args.precision == "c64")
         tickets.append((srv.submit(wl.c, wl.f, wl.N, wl.npml, wl.omega, wl.nbx, wl.nby, wl.overlap, wl.restart,
-                                   wl.rtol, args.max_iters, symmetric=args.storage in ("sym", "auto"),
-                                   tcore=args.storage == "tc",
-                                   reorth=args.reorth), wl))
+                                   wl.rtol, args.max_iters, precision=args.precision,
+                                   symmetric=not tc and args.storage in ("sym", "auto"), tcore=tc,
+                                   reorth=args.reorth, smoothing=args.smoothing), wl))
     lat, solves, ok, unk_it = [], 0, 0, 0.0
     for t, wl in tickets:
         x, stats, info = srv.poll(t)
