@@ -96,14 +96,17 @@ __device__ __forceinline__ void block_argmax(R v, int idx, R *sv, int *si, R &be
   }
   if (lane == 0) { sv[warp] = v; si[warp] = idx; }
   __syncthreads();
-  best = sv[0];
-  bi = si[0];
+  // second level in every warp: lanes 0..7 take the warps' candidates, three shuffles
+  R b2 = lane < FT / 32 ? sv[lane] : (R)-2;
+  int i2 = lane < FT / 32 ? si[lane] : 0x7fffffff;
 #pragma unroll
-  for (int w = 1; w < FT / 32; ++w) {
-    const R ov = sv[w];
-    const int oi = si[w];
-    if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  for (int o = (FT / 32) / 2; o > 0; o >>= 1) {
+    const R ov = __shfl_xor_sync(0xffffffffu, b2, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i2, o);
+    if (ov > b2 || (ov == b2 && oi < i2)) { b2 = ov; i2 = oi; }
   }
+  best = __shfl_sync(0xffffffffu, b2, 0);
+  bi = __shfl_sync(0xffffffffu, i2, 0);
 }
 
 // Storage layouts of the S_j^{-1}: full column-major blocks, upper 16 x 16 tiles,
@@ -241,7 +244,11 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
         T ip;   // reciprocal pivot: one division per warp, broadcast by shuffle
         {
           T inv = mk<T>(0, 0);
-          if ((tid & 31) == 0 && ok) inv = cinv(Pin[t * m + p]);
+          if ((tid & 31) == 0 && ok) {   // one division: 1/|a|^2, then two products
+            const T a = Pin[t * m + p];
+            const R d = (R)1 / fma_rn(a.x, a.x, mul_rn(a.y, a.y));
+            inv = mk<T>(mul_rn(a.x, d), -mul_rn(a.y, d));
+          }
           ip = mk<T>(__shfl_sync(0xffffffffu, inv.x, 0), __shfl_sync(0xffffffffu, inv.y, 0));
         }
         if (tid == 0) {

@@ -541,12 +541,12 @@ template <typename R> __device__ __forceinline__ R smooth_beta(int x, const Axis
 // The sum runs in the compute precision of the local solutions (FP32 for the c64
 // modes: one conversion per cell instead of one per contribution, since the FP64
 // pipe is the scarce one on this GPU) and is written out as complex128.
-template <typename R>
+template <typename R, bool SMOOTH>
 __global__ void __launch_bounds__(256)
 k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const AxisDev *__restrict__ axy,
          const int32_t *__restrict__ nearx, const int32_t *__restrict__ neary, int nbx, int nby,
          const C<R> *__restrict__ staging_all, int64_t stg_stride, double2 *__restrict__ z_all, int64_t vec_stride,
-         int NX, int smooth) {
+         int NX) {
   __shared__ int ylist[3], yoff[3], ny_s;
   __shared__ R ybeta[3];
   const int gy = blockIdx.y;
@@ -559,7 +559,7 @@ k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const
       if (gy >= ay.e0 && gy < ay.e1) {
         ylist[cnt] = jy;
         yoff[cnt] = gy - ay.e0;
-        ybeta[cnt] = smooth_beta<R>(gy, ay);
+        if (SMOOTH) ybeta[cnt] = smooth_beta<R>(gy, ay);
         ++cnt;
       }
     }
@@ -580,7 +580,7 @@ k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const
       if (gx < ax.e0 || gx >= ax.e1) continue;
       const int ex = ax.e1 - ax.e0;
       const C<R> v = staging[subs[jy * nbx + jx].soff + (int64_t)ry * ex + (gx - ax.e0)];
-      if (smooth) {   // beta_ij u_ij (Remark after Eq. (pc))
+      if (SMOOTH) {   // beta_ij u_ij (Remark after Eq. (pc))
         const R b = mul_rn(ybeta[q], smooth_beta<R>(gx, ax));
         acc = mk<C<R>>(fma_rn(b, v.x, acc.x), fma_rn(b, v.y, acc.y));
       } else {
@@ -690,9 +690,10 @@ static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, dou
     if (e != cudaSuccess) return e;
     dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
     tic(ctx, T_GATHER, st);
-    k_gather<R><<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
+    auto gather = ctx->smooth ? k_gather<R, true> : k_gather<R, false>;
+    gather<<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
                                       ctx->nby, reinterpret_cast<const C<R> *>(staging), ctx->staging_elems, z, zs,
-                                      ctx->NX, ctx->smooth ? 1 : 0);
+                                      ctx->NX);
     toc(ctx, T_GATHER, st, 1);
     return cudaGetLastError();
   }
@@ -711,9 +712,10 @@ static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, dou
   if (e != cudaSuccess) return e;
   dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
   tic(ctx, T_GATHER, st);
-  k_gather<R><<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
+  auto gather = ctx->smooth ? k_gather<R, true> : k_gather<R, false>;
+  gather<<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
                                     ctx->nby, reinterpret_cast<const C<R> *>(staging), ctx->staging_elems, z, zs,
-                                    ctx->NX, ctx->smooth ? 1 : 0);
+                                    ctx->NX);
   toc(ctx, T_GATHER, st, 1);
   return cudaGetLastError();
 }
