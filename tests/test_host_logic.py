@@ -1,0 +1,60 @@
+"""Host-side logic that needs no GPU: the seeded workload generators and the
+byte models the bench divides by (roofline numerators)."""
+import numpy as np
+
+import bench
+import workloads as W
+
+
+def test_workloads_are_seeded_and_shaped():
+    a = W.make_workload("precision")
+    b = W.make_workload("precision")
+    assert a.n == 4096 + 32 and a.c.shape == (a.n, a.n) and a.f.shape == (1, a.n, a.n)
+    assert np.array_equal(a.c, b.c) and np.array_equal(a.f, b.f)
+    assert 0.7 - 1e-12 <= a.c.min() and a.c.max() <= 1.3 + 1e-12       # c = 1 + 0.3 clip(g, -1, 1)
+    bt = W.make_workload("batching", nrhs=64)      # the bench asks for its 64 sources
+    assert bt.N == 1984 and bt.nrhs == 64 and bt.nbx == bt.nby == 16
+    peaks = {tuple(np.unravel_index(np.argmax(np.abs(f)), f.shape)) for f in bt.f}
+    assert len(peaks) == 64                       # 64 distinct seeded source positions
+    widths = np.diff(bt.cut_x)
+    assert widths[0] == widths[-1] == 96 and np.all(widths[1:-1] == 128)   # uneven edge boxes
+    md = W.make_workload("medium")
+    assert set(np.unique(md.c)) <= {1.0, 1.5, 2.0}                        # three layers
+
+
+def test_box_extents_match_the_decomposition():
+    """Interior boxes: owned 128 + 2 (overlap 8 + PML 16) = 176; boxes at the edge of
+    the grid: 128 + 16 (global PML owned) + 8 + 16 = 168."""
+    wl = W.make_workload("precision")
+    ext = [bench._extent(wl.cut_x, i, wl) for i in range(wl.nbx)]
+    assert ext[0] == ext[-1] == 168 and all(e == 176 for e in ext[1:-1])
+
+
+def test_block_entries_per_storage():
+    assert bench.block_entries(176, "full") == 176 * 176
+    assert bench.block_entries(176, False) == 176 * 176
+    assert bench.block_entries(176, "sym") == 11 * 12 // 2 * 256          # upper 16x16 tiles
+    assert bench.block_entries(168, "sym") == 11 * 12 // 2 * 256
+    assert bench.block_entries(170, "tc") == 176 * 176                    # rounded up to 8
+    assert bench.block_entries(176, "sym") < 0.55 * 176 * 176
+
+
+def test_subst_bytes_counts_each_block_forward_and_backward():
+    """One box, one source: (2 rows - 1) blocks of the stored entries, the owned residual
+    read once (16 B per cell of the grid) and the staging vector written, read and
+    rewritten (3 rows m c)."""
+    wl = W.make_workload("tiny", N=64, nb=1)
+    m = rows = bench._extent(wl.cut_x, 0, wl)
+    assert m == 64 + 32
+    got = bench.subst_bytes(wl, 8, 1, 8, "full")
+    assert got == 16 * wl.n * wl.n + (2 * rows - 1) * m * m * 8 + 3 * rows * m * 8
+    # 16 sources: groups of 8 per CTA on the CUDA cores (factor read twice), 16 on the tensor cores (once)
+    g16 = bench.subst_bytes(wl, 8, 16, 8, "full") - 16 * (16 * wl.n * wl.n + 3 * rows * m * 8)
+    t16 = bench.subst_bytes(wl, 8, 16, 8, "tc") - 16 * (16 * wl.n * wl.n + 3 * rows * m * 8)
+    assert g16 == 2 * (2 * rows - 1) * m * m * 8 and t16 == (2 * rows - 1) * m * m * 8
+
+
+def test_arnoldi_step_indices_follow_the_cycles():
+    assert bench._arnoldi_js(0, 10) == []
+    assert bench._arnoldi_js(3, 10) == [0, 1, 2]
+    assert bench._arnoldi_js(23, 10) == list(range(10)) * 2 + [0, 1, 2]
