@@ -134,13 +134,13 @@ def make_workload(name: str, N: Optional[int] = None, nb: Optional[int] = None, 
     tiny       128^2, c = 1, Gaussian (w = 2h) at (0.5, 0.5), 2x2 subdomains, GMRES(50) to 1e-8
     medium     1024^2, three horizontal layers c = 1 / 1.5 / 2, Gaussian at a seeded point, 8x8, GMRES(50) to 1e-8
     precision  4096^2, smooth random medium c = 1 + 0.3 g, Gaussian at a seeded point, 32x32, FGMRES(10) to 1e-6
-    batching   1984^2 (owned widths 96 | 14 x 128 | 96), random medium, 64 Gaussian sources, FGMRES(10) to 1e-6
+    batching   1984^2 (owned widths 96 | 14 x 128 | 96), random medium, 64 Gaussian sources, FGMRES(5) to 1e-6
     """
     spec = {
         "tiny": dict(N=128, nb=2, medium="homogeneous", restart=50, rtol=1e-8, seed=0),
         "medium": dict(N=1024, nb=8, medium="three_layer", restart=50, rtol=1e-8, seed=1),
         "precision": dict(N=4096, nb=32, medium="random", restart=10, rtol=1e-6, seed=2),
-        "batching": dict(N=1984, nb=16, medium="random", restart=10, rtol=1e-6, seed=3),
+        "batching": dict(N=1984, nb=16, medium="random", restart=5, rtol=1e-6, seed=3),
     }[name]
     N = N or spec["N"]
     nb = nb or spec["nb"]
