@@ -60,6 +60,41 @@ template <typename T> __device__ __forceinline__ T cinv(T a) {
   auto d = fma_rn(a.x, a.x, mul_rn(a.y, a.y));
   return mk<T>(a.x / d, -a.y / d);
 }
+// FP64 <-> float-pair conversions without conversion instructions, which on this GPU
+// issue at the FP64 pipe's rate (1/64 of FP32).  ds_split(x) = (h, l): h is x truncated
+// to 24 significant bits (its bits moved into float fields), l = x - h rounded to float.
+// The 29 bits below h are turned into floats by the exponent trick: a float with
+// exponent field E and mantissa field q is 2^(E-127) + q 2^(E-150), so subtracting
+// 2^(E-127) leaves q 2^(E-150) exactly; the top 23 and the low 6 of the 29 bits each
+// take one such subtraction and one rounded FP32 add joins them (|x - h - l| <= 2^-47
+// |x|).  Valid for FP64 exponents 949..1150 (|x| in [2^-74, 2^128)), where every
+// intermediate float is normal; zero and FP64 subnormals give (0, 0), everything else
+// (tiny, huge, inf, NaN) takes the conversion instructions.
+__device__ __forceinline__ float2 ds_split(double x) {
+  const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+  const unsigned int e = (hi >> 20) & 0x7FFu;
+  if (e - 949u > 1150u - 949u) {
+    if (e == 0u) return make_float2(0.f, 0.f);
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+  }
+  const unsigned int sg = hi & 0x80000000u;
+  const unsigned int eh = (e - 896u) << 23;                                  // float exponent field of h
+  const float h = __uint_as_float(sg | eh | (__funnelshift_l(lo, hi, 3) & 0x7FFFFFu));
+  const unsigned int e1 = sg | (eh - (23u << 23)), e0 = sg | (eh - (29u << 23));
+  const float l1 = __fsub_rn(__uint_as_float(e1 | ((lo >> 6) & 0x7FFFFFu)), __uint_as_float(e1));
+  const float l0 = __fsub_rn(__uint_as_float(e0 | (lo & 63u)), __uint_as_float(e0));
+  return make_float2(h, __fadd_rn(l1, l0));
+}
+// float -> FP64 by moving the fields (exact); zero gives 0, subnormals, inf and NaN convert.
+__device__ __forceinline__ double ds_f2d(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int e = (u >> 23) & 0xFFu;
+  if (e - 1u > 253u) return (u << 1) == 0u ? 0.0 : (double)f;
+  return __hiloint2double((int)((u & 0x80000000u) | ((e + 896u) << 20) | ((u & 0x7FFFFFu) >> 3)), (int)(u << 29));
+}
+// h + l in FP64: one FP64 add.
+__device__ __forceinline__ double ds_to_d(float h, float l) { return ds_f2d(h) + ds_f2d(l); }
 __host__ __device__ __forceinline__ float2 to_c(double2 z, float2) { return make_float2((float)z.x, (float)z.y); }
 __host__ __device__ __forceinline__ double2 to_c(double2 z, double2) { return z; }
 __host__ __device__ __forceinline__ double2 to_d(float2 z) { return make_double2(z.x, z.y); }

@@ -181,13 +181,10 @@ __global__ void __launch_bounds__(256) k_scale(const double2 *__restrict__ w_all
 // ALU-bound.  In this mode the basis V is stored as pairs of floats (hi, lo)
 // with hi + lo equal to the FP64 value to about 2^-48, and the dot products
 // and updates use double-single arithmetic (Dekker/Knuth error-free products
-// and sums on the FP32 pipes).  The FP64 copy of the newest basis vector feeds
-// the preconditioner; the residuals, norms, Hessenberg and Givens work stay FP64.
-__device__ __forceinline__ float2 split_d(double x) {
-  float h = __double2float_rn(x);
-  float l = __double2float_rn(x - (double)h);
-  return make_float2(h, l);
-}
+// and sums on the FP32 pipes), and the conversions between FP64 and float pairs
+// move bit fields instead of issuing conversion instructions (ds_split, ds_f2d).
+// The FP64 copy of the newest basis vector feeds the preconditioner; the
+// residuals, Hessenberg and Givens work stay FP64, the norms are double-single.
 
 // (sh, sl) += (ah + al)(bh + bl), error-free hi product, FP32 cross terms.
 __device__ __forceinline__ void ds_mac(float &sh, float &sl, float ah, float al, float bh, float bl) {
@@ -235,7 +232,7 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, i
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < cnt) {
       double2 x = w[base + i];
-      float2 r = split_d(x.x), m = split_d(x.y);
+      float2 r = ds_split(x.x), m = ds_split(x.y);
       v = make_float4(r.x, r.y, m.x, m.y);
     }
     wsm[i] = v;
@@ -271,7 +268,7 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, i
       ds_add(rh, rl, a, b);
       ds_add(ih, il, c, d);
     }
-    if (lane == 0) partial[(int64_t)k * G + blockIdx.x] = make_double2((double)rh + (double)rl, (double)ih + (double)il);
+    if (lane == 0) partial[(int64_t)k * G + blockIdx.x] = make_double2(ds_to_d(rh, rl), ds_to_d(ih, il));
   }
 }
 
@@ -301,7 +298,7 @@ __global__ void __launch_bounds__(256) k_dots_df_few(const float4 *__restrict__ 
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (i < cnt) {
       const double2 x = w[base + i];
-      const float2 r = split_d(x.x), m = split_d(x.y);
+      const float2 r = ds_split(x.x), m = ds_split(x.y);
       v = make_float4(r.x, r.y, m.x, m.y);
     }
     wv[u] = v;
@@ -344,7 +341,7 @@ __global__ void __launch_bounds__(256) k_dots_df_few(const float4 *__restrict__ 
       ds_add(t.x, t.y, o.x, o.y);
       ds_add(t.z, t.w, o.z, o.w);
     }
-    partial[(int64_t)tid * G + blockIdx.x] = make_double2((double)t.x + (double)t.y, (double)t.z + (double)t.w);
+    partial[(int64_t)tid * G + blockIdx.x] = make_double2(ds_to_d(t.x, t.y), ds_to_d(t.z, t.w));
   }
 }
 
@@ -366,13 +363,13 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
   double2 *y = y_all + (int64_t)r * ldy;
   for (int k = tid; k < nk; k += DT) {
     double2 c = coef[k];
-    float2 cr = split_d(c.x), ci = split_d(c.y);
+    float2 cr = ds_split(c.x), ci = ds_split(c.y);
     csm[k] = make_float4(cr.x, cr.y, ci.x, ci.y);
   }
   __syncthreads();
   constexpr int E = 4;
   const int64_t b0 = (int64_t)blockIdx.x * DCHUNK + tid;
-  double nrm = 0.0;
+  float nh = 0.f, nl = 0.f;   // double-single |y|^2 of this thread's elements
 #pragma unroll 1
   for (int half = 0; half < DE / E; ++half) {
     float rh[E], rl[E], ih[E], il[E];
@@ -404,14 +401,23 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
     for (int e = 0; e < E; ++e) {
       int64_t i = b0 + (int64_t)DT * (half * E + e);
       if (i < n) {
-        double2 bv = base[i];
-        double2 o = make_double2(bv.x - ((double)rh[e] + (double)rl[e]), bv.y - ((double)ih[e] + (double)il[e]));
-        y[i] = o;
-        if (NORM) nrm += o.x * o.x + o.y * o.y;
+        // y = base - acc in double-single, then one FP64 add per component
+        const double2 bv = base[i];
+        const float2 br = ds_split(bv.x), bi = ds_split(bv.y);
+        float oh = br.x, ol = br.y, qh = bi.x, ql = bi.y;
+        ds_add(oh, ol, -rh[e], -rl[e]);
+        ds_add(qh, ql, -ih[e], -il[e]);
+        y[i] = make_double2(ds_to_d(oh, ol), ds_to_d(qh, ql));
+        if (NORM) {
+          ds_mac(nh, nl, oh, ol, oh, ol);
+          ds_mac(nh, nl, qh, ql, qh, ql);
+        }
       }
     }
+    if (NORM) ds_renorm(nh, nl);
   }
   if (NORM) {
+    double nrm = ds_to_d(nh, nl);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
     if ((tid & 31) == 0) nsm[tid >> 5] = nrm;
@@ -446,7 +452,7 @@ __global__ void __launch_bounds__(256) k_scale_df(const double2 *__restrict__ w_
     const int64_t i = i0 + 256 * u;
     if (i >= n) break;
     const double2 v = make_double2(a[u].x * inv, a[u].y * inv);
-    const float2 cr = split_d(v.x), ci = split_d(v.y);
+    const float2 cr = ds_split(v.x), ci = ds_split(v.y);
     vout_all[(int64_t)r * ldvr + i] = make_float4(cr.x, cr.y, ci.x, ci.y);
     vin_all[(int64_t)r * n + i] = v;
   }
