@@ -80,7 +80,7 @@ def parse():
     p.add_argument("--probe-peaks", action="store_true", help="also measure FP64/FP32 FMA and copy rates")
     p.add_argument("--npml", type=int, default=None, help="PML cells per side (default 16)")
     p.add_argument("--nrhs", type=int, default=None, help="sources per solve (batching config: 64)")
-    p.add_argument("--group", type=int, default=16, help="sources solved together in lockstep")
+    p.add_argument("--group", type=int, default=64, help="sources solved together in lockstep (default: all of the batching workload)")
     p.add_argument("--single-sample", type=int, default=2, help="batching: sources also solved one at a time")
     return p.parse_args()
 

@@ -117,9 +117,9 @@ k_subst(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const
   using T = C<R>;
   constexpr int CH = chunk_cols<S>();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const SubDev s = subs[blockIdx.x];
+  const SubDev s = subs[blockIdx.y];
   const int m = s.ex, rows = s.ey, ldm = s.ldm;
-  const int r0 = blockIdx.y * NR;
+  const int r0 = blockIdx.x * NR;
   const size_t stage_elems = (size_t)CH * ldmax;
   S *ring = reinterpret_cast<S *>(smem_raw);
   T *vs = reinterpret_cast<T *>(ring + (size_t)NS * stage_elems);     // [NR][ldmax]
@@ -332,11 +332,11 @@ k_subst_sym(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, c
   constexpr int TPC = NW * TPW;   // tiles per ring stage
   constexpr int TE = TB * TB;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const SubDev s = subs[blockIdx.x];
+  const SubDev s = subs[blockIdx.y];
   const int m = s.ex, rows = s.ey;
   const int mt = (m + TB - 1) / TB, mp = mt * TB, nt = mt * (mt + 1) / 2;
   const int ntmax = (mpmax / TB) * (mpmax / TB + 1) / 2;
-  const int r0 = blockIdx.y * NR;
+  const int r0 = blockIdx.x * NR;
   S *ring = reinterpret_cast<S *>(smem_raw);
   T *vs = reinterpret_cast<T *>(ring + (size_t)NS * TPC * TE);   // [NR][mpmax]
   T *part = vs + (size_t)NR * mpmax;                               // [NW][NR][mpmax]
@@ -621,7 +621,7 @@ static cudaError_t launch_subst(hd_ctx *ctx, const double2 *r, int nrhs, int64_t
   const size_t smem = subst_smem<T, S>(ns, ldmax, NR);
   cudaError_t e = cudaFuncSetAttribute(k_subst<R, S, CT, NA, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(ctx->nsub, groups);
+  dim3 grid(groups, ctx->nsub);   // a box's source groups run side by side and share its factor reads in L2
   k_subst<R, S, CT, NA, NR><<<grid, CT + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,
                                                         reinterpret_cast<const S *>(ctx->factor), r, ctx->NX,
                                                         vec_stride, reinterpret_cast<T *>(staging), stg_stride, nrhs,
@@ -658,7 +658,7 @@ static cudaError_t launch_subst_sym(hd_ctx *ctx, const double2 *r, int nrhs, int
   const size_t smem = subst_sym_smem<T, S>(ns, mpmax, NW, NR, ntmax);
   cudaError_t e = cudaFuncSetAttribute(k_subst_sym<R, S, NW, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(ctx->nsub, groups);
+  dim3 grid(groups, ctx->nsub);   // a box's source groups run side by side and share its factor reads in L2
   k_subst_sym<R, S, NW, NR><<<grid, NW * 32 + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,
                                                               reinterpret_cast<const S *>(ctx->factor), r, ctx->NX,
                                                               vec_stride, reinterpret_cast<T *>(staging), stg_stride,

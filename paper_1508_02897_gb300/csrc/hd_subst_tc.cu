@@ -129,9 +129,9 @@ k_subst_tc(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, co
            const double2 *__restrict__ rg, int NX, int64_t vec_stride, float2 *__restrict__ staging, int64_t stg_stride,
            int nrhs, int NS, int mp8max, int32_t *status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const SubDev s = subs[blockIdx.x];
+  const SubDev s = subs[blockIdx.y];
   const int m = s.ex, rows = s.ey, mp8 = (m + 7) & ~7;
-  const int r0 = blockIdx.y * TC_NR;
+  const int r0 = blockIdx.x * TC_NR;
   const size_t stage_bytes = (size_t)64 * mp8max;
   unsigned char *A1 = smem_raw;
   unsigned char *A2 = A1 + (size_t)kBLbo * mp8max;
@@ -395,7 +395,9 @@ cudaError_t launch_subst_tc(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec
   const size_t smem = subst_tc_smem(ns, mp8max);
   cudaError_t e = cudaFuncSetAttribute(k_subst_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(ctx->nsub, groups);
+  // the groups of one box are neighbours in launch order: they run together and read
+  // the box's factor chunks at about the same time, so L2 serves most repeated reads
+  dim3 grid(groups, ctx->nsub);
   k_subst_tc<<<grid, TC_THREADS, smem, st>>>(ctx->d_subs, ctx->d_lpool, reinterpret_cast<const float *>(ctx->factor), r,
                                              ctx->NX, vec_stride, reinterpret_cast<float2 *>(staging), stg_stride,
                                              nrhs, ns, mp8max, ctx->d_status);

@@ -169,10 +169,13 @@ def _sources(case, k, seed):
     return np.stack([W.gaussian_source(N, npml, *rng.uniform(0.15, 0.85, 2), 2.0 / N) for _ in range(k)])
 
 
-@pytest.mark.parametrize("precision,nrhs", [("c128", 3), ("c64", 9), ("c64s", 5), ("c64t", 5), ("c64t", 19)])
+@pytest.mark.parametrize("precision,nrhs", [("c128", 3), ("c64", 9), ("c64s", 5), ("c64t", 5), ("c64t", 19),
+                                             ("c64t", 37)])
 def test_precond_batched_equals_single(precision, nrhs):
     """Each right-hand side of a batched application (groups of up to 8 per CTA, 16
-    on the tensor cores) gives bitwise the same vector as its own application."""
+    on the tensor cores; 37 sources there give two full groups and a ragged one of 5,
+    launched side by side per box) gives bitwise the same vector as its own
+    application."""
     _, _, g, _, P = oracle("ragged")
     s = gpu("ragged", precision)
     r = W.random_complex((nrhs, g.n, g.n), seed=12)

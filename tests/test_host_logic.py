@@ -52,6 +52,9 @@ def test_subst_bytes_counts_each_block_forward_and_backward():
     g16 = bench.subst_bytes(wl, 8, 16, 8, "full") - 16 * (16 * wl.n * wl.n + 3 * rows * m * 8)
     t16 = bench.subst_bytes(wl, 8, 16, 8, "tc") - 16 * (16 * wl.n * wl.n + 3 * rows * m * 8)
     assert g16 == 2 * (2 * rows - 1) * m * m * 8 and t16 == (2 * rows - 1) * m * m * 8
+    # 64 sources: 8 groups on the CUDA cores, 4 of 16 on the tensor cores
+    t64 = bench.subst_bytes(wl, 8, 64, 8, "tc") - 64 * (16 * wl.n * wl.n + 3 * rows * m * 8)
+    assert t64 == 4 * (2 * rows - 1) * m * m * 8
 
 
 def test_arnoldi_step_indices_follow_the_cycles():
