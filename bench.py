@@ -335,18 +335,22 @@ def run_ours(args, world, rank, local):
     # Arnoldi: each Gram-Schmidt pass is one dot pass and one update pass over the
     # j+1 basis vectors; the first pass always runs, the second as counted by the
     # solver.  FP64 flops (8 per complex multiply-add) and bytes (16 per entry and
-    # pass; w is read by the dots, read and written by the update, and the scaling
-    # reads w and writes v_{j+1}).
+    # pass).  FP64 mode: w is read by the dots, read and written by the update, and the
+    # scaling reads w and writes v_{j+1} (5 vector passes besides the basis; 3 in a second
+    # pass).  Double-single mode normalises lazily: the dots read w, the update reads w
+    # and writes the new vector twice (float pairs into the basis, FP64 for the
+    # preconditioner), 4 vector passes in either pass.
+    ds_mode = args.arnoldi == "ds" or (args.arnoldi == "auto" and args.precision != "c128")
+    first_vecs, second_vecs = (4, 4) if ds_mode else (5, 3)
     arn_flops = arn_bytes = 0
     for it_total in iters:
         for j in _arnoldi_js(it_total, wl.restart):
             arn_flops += 16 * (j + 1) * n_unk
-            arn_bytes += 2 * (j + 1) * n_unk * 16 + 5 * n_unk * 16
+            arn_bytes += 2 * (j + 1) * n_unk * 16 + first_vecs * n_unk * 16
     for s_ in stats:
         arn_flops += 16 * s_["second_pass_vecs"] * n_unk
-        arn_bytes += 2 * s_["second_pass_vecs"] * n_unk * 16 + 3 * s_["second_passes"] * n_unk * 16
+        arn_bytes += 2 * s_["second_pass_vecs"] * n_unk * 16 + second_vecs * s_["second_passes"] * n_unk * 16
     arn_s = cls_ms["arnoldi"] / 1e3
-    ds_mode = args.arnoldi == "ds" or (args.arnoldi == "auto" and args.precision != "c128")
 
     out = {
         "metric": METRIC, "value": solves / total_max_s, "unit": "solves/s", "n_gpus": world,

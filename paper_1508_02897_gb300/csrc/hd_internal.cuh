@@ -95,6 +95,32 @@ __device__ __forceinline__ double ds_f2d(float f) {
 }
 // h + l in FP64: one FP64 add.
 __device__ __forceinline__ double ds_to_d(float h, float l) { return ds_f2d(h) + ds_f2d(l); }
+// (sh, sl) += (ah + al)(bh + bl), error-free hi product, FP32 cross terms.
+__device__ __forceinline__ void ds_mac(float &sh, float &sl, float ah, float al, float bh, float bl) {
+  float p = __fmul_rn(ah, bh);
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, fmaf(al, bh, e));
+  float t = __fadd_rn(sh, p);
+  float z = __fsub_rn(t, sh);
+  float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ void ds_renorm(float &sh, float &sl) {
+  float t = __fadd_rn(sh, sl);
+  sl = __fsub_rn(sl, __fsub_rn(t, sh));
+  sh = t;
+}
+
+__device__ __forceinline__ void ds_add(float &sh, float &sl, float bh, float bl) {
+  float t = __fadd_rn(sh, bh);
+  float z = __fsub_rn(t, sh);
+  float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(bh, z));
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(err, bl));
+  ds_renorm(sh, sl);
+}
 __host__ __device__ __forceinline__ float2 to_c(double2 z, float2) { return make_float2((float)z.x, (float)z.y); }
 __host__ __device__ __forceinline__ double2 to_c(double2 z, double2) { return z; }
 __host__ __device__ __forceinline__ double2 to_d(float2 z) { return make_double2(z.x, z.y); }

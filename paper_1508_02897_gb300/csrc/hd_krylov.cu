@@ -186,33 +186,6 @@ __global__ void __launch_bounds__(256) k_scale(const double2 *__restrict__ w_all
 // The FP64 copy of the newest basis vector feeds the preconditioner; the
 // residuals, Hessenberg and Givens work stay FP64, the norms are double-single.
 
-// (sh, sl) += (ah + al)(bh + bl), error-free hi product, FP32 cross terms.
-__device__ __forceinline__ void ds_mac(float &sh, float &sl, float ah, float al, float bh, float bl) {
-  float p = __fmul_rn(ah, bh);
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, fmaf(al, bh, e));
-  float t = __fadd_rn(sh, p);
-  float z = __fsub_rn(t, sh);
-  float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(p, z));
-  sh = t;
-  sl = __fadd_rn(sl, __fadd_rn(err, e));
-}
-
-__device__ __forceinline__ void ds_renorm(float &sh, float &sl) {
-  float t = __fadd_rn(sh, sl);
-  sl = __fsub_rn(sl, __fsub_rn(t, sh));
-  sh = t;
-}
-
-__device__ __forceinline__ void ds_add(float &sh, float &sl, float bh, float bl) {
-  float t = __fadd_rn(sh, bh);
-  float z = __fsub_rn(t, sh);
-  float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, z)), __fsub_rn(bh, z));
-  sh = t;
-  sl = __fadd_rn(sl, __fadd_rn(err, bl));
-  ds_renorm(sh, sl);
-}
-
 // partial[r][k][blk] = sum over the block's DFC elements of conj(V_r[k][i]) w_r[i].
 // With `self`, entry nk is ||w_r||^2; with skip[r] set, the block does nothing.
 __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk0,
@@ -345,24 +318,32 @@ __global__ void __launch_bounds__(256) k_dots_df_few(const float4 *__restrict__ 
   }
 }
 
-// y_r = base_r - sum_k V_r[k] coef_r[k] (double-single accumulation, FP64 result);
-// optionally normpart[r][blk] = block sum of |y_r|^2.
+// y_r = base_r - sum_k V_r[k] coef_r[k] sc_r[k]^2 (double-single accumulation): the stored
+// basis vectors are u_k = v_k / sc_k (normalised lazily, see k_arnoldi_step), so the
+// projection on v_k takes coef sc_k^2.  y_r goes to the basis slot vout_r as float pairs
+// and to y_r in FP64 (the preconditioner's input); optionally normpart[r][blk] = block
+// sum of |y_r|^2.
 template <bool NORM>
 __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
-                                                  const double2 *__restrict__ coef_all, int ldc, const double2 *base_all,
-                                                  double2 *y_all, int64_t ldy, int64_t n,
-                                                  double2 *__restrict__ normpart_all, int64_t ldp,
+                                                  const double2 *__restrict__ coef_all, int ldc,
+                                                  const double *__restrict__ sc_all, const double2 *base_all,
+                                                  double2 *y_all, int64_t ldy, float4 *__restrict__ vout_all,
+                                                  int64_t n, double2 *__restrict__ normpart_all, int64_t ldp,
                                                   const int *__restrict__ skip) {
   extern __shared__ float4 csm[];  // [nk]
   __shared__ double nsm[DT / 32];
   const int tid = threadIdx.x, r = blockIdx.y;
   if (skip && skip[r]) return;
   const double2 *coef = coef_all + (int64_t)r * ldc;
+  const double *sc = sc_all + (int64_t)r * ldc;
   const float4 *Vr = V + (int64_t)r * ldvr;
   const double2 *base = base_all + (int64_t)r * ldy;
   double2 *y = y_all + (int64_t)r * ldy;
+  float4 *vout = vout_all + (int64_t)r * ldvr;
   for (int k = tid; k < nk; k += DT) {
-    double2 c = coef[k];
+    const double2 c0 = coef[k];
+    const double s2 = sc[k] * sc[k];
+    const double2 c = make_double2(c0.x * s2, c0.y * s2);
     float2 cr = ds_split(c.x), ci = ds_split(c.y);
     csm[k] = make_float4(cr.x, cr.y, ci.x, ci.y);
   }
@@ -408,6 +389,7 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
         ds_add(oh, ol, -rh[e], -rl[e]);
         ds_add(qh, ql, -ih[e], -il[e]);
         y[i] = make_double2(ds_to_d(oh, ol), ds_to_d(qh, ql));
+        vout[i] = make_float4(oh, ol, qh, ql);
         if (NORM) {
           ds_mac(nh, nl, oh, ol, oh, ol);
           ds_mac(nh, nl, qh, ql, qh, ql);
@@ -470,7 +452,9 @@ struct GmresDev {
   double *stat;      // [nrhs][4] host-visible summary: |g_{j+1}|, h_{j+1,j}, non-finite flag
   int *live;         // [nrhs] 1 while the right-hand side takes Arnoldi steps
   int *kcnt;         // [nrhs] Arnoldi steps of the current cycle
+  double *sc;        // [nrhs][ldh] lazy normalisation: basis vector k is stored as v_k / sc_k
   int ldh, restart, nrhs;
+  int lazy;          // 1: stored basis vectors carry the scales sc (double-single mode)
 };
 
 __device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, a.y); }
@@ -491,6 +475,7 @@ __global__ void k_cycle_init(GmresDev d) {
   if (r >= d.nrhs) return;
   const double beta = sqrt(d.red[4 * r].x);
   d.red[4 * r + 1] = make_double2(beta > 0.0 ? 1.0 / beta : 0.0, 0.0);
+  d.sc[(int64_t)r * d.ldh] = 1.0;   // v_0 = r / beta is stored normalised
   if (!d.live[r]) return;
   double2 *g = d.g + (int64_t)r * d.ldh;
   for (int i = 0; i < d.ldh; ++i) g[i] = make_double2(0.0, 0.0);
@@ -498,6 +483,10 @@ __global__ void k_cycle_init(GmresDev d) {
 }
 
 // Column j of H from the two CGS passes, old rotations, new rotation, g update.
+// Lazy normalisation (double-single mode): the stored vectors are u_k = v_k / sc_k and
+// the preconditioner ran on u_j, so w = A M u_j = (A z_j) / sc_j, the passes returned
+// u_k^H w, and the vector left over is y = (A z_j - sum_k h_kj v_k) / sc_j; hence
+// h_kj = sc_j sc_k (h1_k + h2_k), h_{j+1,j} = sc_j ||y|| and sc_{j+1} = 1 / ||y||.
 __global__ void k_arnoldi_step(GmresDev d, int j) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= d.nrhs || !d.live[r]) return;
@@ -510,8 +499,20 @@ __global__ void k_arnoldi_step(GmresDev d, int j) {
   }
   double2 *sn = d.sn + (int64_t)r * d.restart;
   double2 *g = d.g + (int64_t)r * d.ldh;
-  for (int i = 0; i <= j; ++i) Hj[i] = cadd(h1[i], h2[i]);
   double hn = sqrt(d.red[4 * r].x);
+  if (d.lazy) {
+    double *sc = d.sc + (int64_t)r * d.ldh;
+    const double sj = sc[j];
+    for (int i = 0; i <= j; ++i) {
+      const double2 h = cadd(h1[i], h2[i]);
+      const double f = sj * sc[i];
+      Hj[i] = make_double2(f * h.x, f * h.y);
+    }
+    sc[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
+    hn *= sj;
+  } else {
+    for (int i = 0; i <= j; ++i) Hj[i] = cadd(h1[i], h2[i]);
+  }
   Hj[j + 1] = make_double2(hn, 0.0);
   for (int i = 0; i < j; ++i) {
     double c = cs[i];
@@ -566,6 +567,10 @@ __global__ void k_trisolve(GmresDev d) {
     for (int l = i + 1; l < k; ++l) acc = cfms(H[(int64_t)l * d.ldh + i], y[l], acc);
     y[i] = cmul(acc, cinv(H[(int64_t)i * d.ldh + i]));
   }
+  if (d.lazy) {   // the stored z'_i = M u_i = z_i / sc_i
+    const double *sc = d.sc + (int64_t)r * d.ldh;
+    for (int i = 0; i < k; ++i) y[i] = make_double2(y[i].x * sc[i], y[i].y * sc[i]);
+  }
 }
 
 // ---------------------------------------------------------------- workspace
@@ -575,7 +580,7 @@ struct KrylovLayout {
   int64_t n;
   int restart, nrhs, G, Gdf, Gmax;
   size_t off_V, off_Z, off_w, off_vin, off_part, off_h1, off_h2, off_red, off_H, off_cs, off_sn, off_g, off_y,
-      off_stat, off_live, off_ddm, total;
+      off_stat, off_live, off_sc, off_ddm, total;
 };
 
 static KrylovLayout krylov_layout(int64_t n, int restart, int nrhs) {
@@ -601,6 +606,7 @@ static KrylovLayout krylov_layout(int64_t n, int restart, int nrhs) {
   L.off_y = o; o += al(c16 * R * B);
   L.off_stat = o; o += al(sizeof(double) * 4 * B);
   L.off_live = o; o += al(sizeof(int) * 3 * B);   // live [B], kcnt [B], skip [B]
+  L.off_sc = o; o += al(sizeof(double) * (R + 1) * B);
   L.off_ddm = o; o += al(c16 * 2 * n * B);       // multi-step DDM: residual and correction
   L.total = o;
   return L;
@@ -674,16 +680,19 @@ struct Krylov {
     toc(ctx, T_ARNOLDI, st, 2);
     return cudaGetLastError();
   }
-  cudaError_t update_df(int nk, const double2 *coef, int ldc, double2 *wv, double2 *norm_out, const int *skip = nullptr) {
+  // y = base - V (coef sc^2) into vin (FP64) and into basis slot nk (float pairs)
+  cudaError_t update_df(int nk, const double2 *coef, int ldc, const double *sc, const double2 *base,
+                        double2 *norm_out, const int *skip = nullptr) {
     tic(ctx, T_ARNOLDI, st);
     size_t sm = sizeof(float4) * nk;
+    float4 *vout = Vdf() + (int64_t)nk * L.n;
     if (norm_out) {
-      k_update_df<true><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, wv, wv, L.n, L.n, part(), ldp(),
-                                                      skip);
+      k_update_df<true><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, sc, base, vin(), L.n, vout,
+                                                      L.n, part(), ldp(), skip);
       k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4, skip, 2);
     } else {
-      k_update_df<false><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, wv, wv, L.n, L.n, nullptr, 0,
-                                                       skip);
+      k_update_df<false><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, sc, base, vin(), L.n, vout,
+                                                       L.n, nullptr, 0, skip);
     }
     toc(ctx, T_ARNOLDI, st, norm_out ? 2 : 1);
     return cudaGetLastError();
@@ -727,11 +736,13 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
   d.red = K.at<double2>(K.L.off_red);
   d.stat = K.at<double>(K.L.off_stat);
   d.live = K.at<int>(K.L.off_live);
+  d.sc = K.at<double>(K.L.off_sc);
   d.kcnt = d.live + B;
   int *skip = d.live + 2 * B;
   const bool sel = o->reorth == 1;
   d.ldh = R + 1; d.restart = R; d.nrhs = B;
   const bool dsm = o->arnoldi == HD_ARNOLDI_DS;
+  d.lazy = dsm ? 1 : 0;
   if (dsm) KCHK(cudaFuncSetAttribute(k_dots_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(float4) * DFC)));
   const dim3 gs((unsigned)((n + 255) / 256), B);
   const dim3 gsc((unsigned)((n + 256 * SCE - 1) / (256 * SCE)), B);
@@ -806,19 +817,21 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
       int rc2 = run_apply_steps(ctx, vj, vjs, zj, zs, B, std::max(1, o->precond_steps), K.at<double2>(K.L.off_ddm),
                                 scratch, st);
       if (rc2) return rc2;
-      tic(ctx, T_MATVEC, st);
-      KCHK(launch_matvec(ctx, zj, zs, K.w(), n, B, st));
-      toc(ctx, T_MATVEC, st, 1);
       // CGS2: h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2; with selective
       // reorthogonalisation the second pass is skipped (h2 = 0) unless the first
       // cancelled more than a factor 10 of ||w||.
       const int self = sel ? 1 : 0;
+      tic(ctx, T_MATVEC, st);
+      KCHK(launch_matvec(ctx, zj, zs, K.w(), n, B, st));
+      toc(ctx, T_MATVEC, st, 1);
       if (dsm) {
+        // the vector left after each pass goes straight to vin and basis slot j + 1,
+        // unnormalised (k_arnoldi_step records its scale)
         KCHK(K.dots_df(j + 1, K.w(), d.h1, R + 1, nullptr, self));
-        KCHK(K.update_df(j + 1, d.h1, R + 1, K.w(), sel ? d.red : nullptr));
+        KCHK(K.update_df(j + 1, d.h1, R + 1, d.sc, K.w(), sel ? d.red : nullptr));
         if (sel) k_reorth_decide<<<nb, tb, 0, st>>>(d, j + 1, skip);
-        KCHK(K.dots_df(j + 1, K.w(), d.h2, R + 1, sel ? skip : nullptr));
-        KCHK(K.update_df(j + 1, d.h2, R + 1, K.w(), d.red, sel ? skip : nullptr));
+        KCHK(K.dots_df(j + 1, K.vin(), d.h2, R + 1, sel ? skip : nullptr));
+        KCHK(K.update_df(j + 1, d.h2, R + 1, d.sc, K.vin(), d.red, sel ? skip : nullptr));
       } else {
         KCHK(K.dots(K.V(), K.ldvr(), j + 1, K.w(), d.h1, R + 1, nullptr, self));
         KCHK(K.update(K.V(), K.ldvr(), j + 1, nullptr, d.h1, R + 1, -1.0, K.w(), K.w(), sel ? d.red : nullptr));
@@ -829,9 +842,8 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
       if (sel) ctx->t_launch[T_ARNOLDI] += 1;
       tic(ctx, T_ARNOLDI, st);
       k_arnoldi_step<<<nb, tb, 0, st>>>(d, j);
-      if (dsm) k_scale_df<<<gsc, 256, 0, st>>>(K.w(), n, d.red, K.Vdf() + (int64_t)(j + 1) * n, K.ldvr(), K.vin(), n);
-      else k_scale<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.V() + (int64_t)(j + 1) * n, K.ldvr(), n);
-      toc(ctx, T_ARNOLDI, st, 2);
+      if (!dsm) k_scale<<<gs, 256, 0, st>>>(K.w(), n, d.red, K.V() + (int64_t)(j + 1) * n, K.ldvr(), n);
+      toc(ctx, T_ARNOLDI, st, dsm ? 1 : 2);
       KCHK(cudaGetLastError());
       return HD_OK;
     };
