@@ -510,7 +510,7 @@ def _profile_traffic(wl, args):
         return None
 
 
-KERNEL_REV = {False: "subst-v3", True: "subst-sym-v2"}   # kernel revisions the traffic summaries describe
+KERNEL_REV = {False: "subst-v4", True: "subst-sym-v3"}   # kernel revisions the traffic summaries describe
 
 
 # ----------------------------------------------------------------------------- serving
