@@ -187,13 +187,14 @@ __global__ void __launch_bounds__(256) k_scale(const double2 *__restrict__ w_all
 // residuals, Hessenberg and Givens work stay FP64, the norms are double-single.
 
 // partial[r][k][blk] = sum over the block's DFC elements of conj(V_r[k][i]) w_r[i].
-// With `self`, entry nk is ||w_r||^2; with skip[r] set, the block does nothing.
+// With `self`, entry nk is ||w_r||^2; with skip[r] set or live[r] clear (a right-hand
+// side of a lockstep batch that has stopped), the block does nothing.
 __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk0,
                                                  const double2 *__restrict__ w_all, int64_t ldw, int64_t n,
                                                  double2 *__restrict__ partial_all, int G, int64_t ldp,
-                                                 const int *__restrict__ skip, int self) {
+                                                 const int *__restrict__ skip, const int *__restrict__ live, int self) {
   extern __shared__ float4 wsm[];  // [DFC]
-  if (skip && skip[blockIdx.y]) return;
+  if ((skip && skip[blockIdx.y]) || (live && !live[blockIdx.y])) return;
   const int nk = nk0 + self;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t base = (int64_t)blockIdx.x * DFC;
@@ -253,9 +254,10 @@ template <int KM>
 __global__ void __launch_bounds__(256) k_dots_df_few(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk0,
                                                      const double2 *__restrict__ w_all, int64_t ldw, int64_t n,
                                                      double2 *__restrict__ partial_all, int G, int64_t ldp,
-                                                     const int *__restrict__ skip, int self) {
+                                                     const int *__restrict__ skip, const int *__restrict__ live,
+                                                     int self) {
   __shared__ float4 red[8][KM];
-  if (skip && skip[blockIdx.y]) return;
+  if ((skip && skip[blockIdx.y]) || (live && !live[blockIdx.y])) return;
   const int nk = nk0 + self;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t base = (int64_t)blockIdx.x * DFC;
@@ -329,11 +331,11 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
                                                   const double *__restrict__ sc_all, const double2 *base_all,
                                                   double2 *y_all, int64_t ldy, float4 *__restrict__ vout_all,
                                                   int64_t n, double2 *__restrict__ normpart_all, int64_t ldp,
-                                                  const int *__restrict__ skip) {
+                                                  const int *__restrict__ skip, const int *__restrict__ live) {
   extern __shared__ float4 csm[];  // [nk]
   __shared__ double nsm[DT / 32];
   const int tid = threadIdx.x, r = blockIdx.y;
-  if (skip && skip[r]) return;
+  if ((skip && skip[r]) || (live && !live[r])) return;
   const double2 *coef = coef_all + (int64_t)r * ldc;
   const double *sc = sc_all + (int64_t)r * ldc;
   const float4 *Vr = V + (int64_t)r * ldvr;
@@ -627,6 +629,7 @@ struct Krylov {
   KrylovLayout L;
   char *ws;
   int B;
+  const int *live = nullptr;   // double-single kernels skip right-hand sides with live[r] == 0
   template <typename T> T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
   double2 *V() const { return at<double2>(L.off_V); }
   float4 *Vdf() const { return at<float4>(L.off_V); }
@@ -668,14 +671,17 @@ struct Krylov {
     tic(ctx, T_ARNOLDI, st);
     const dim3 grid(L.Gdf, B);
     if (nk + self <= 4)
-      k_dots_df_few<4><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, self);
+      k_dots_df_few<4><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, live,
+                                                 self);
     else if (nk + self <= 8)
-      k_dots_df_few<8><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, self);
+      k_dots_df_few<8><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, live,
+                                                 self);
     else if (nk + self <= 12)
-      k_dots_df_few<12><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, self);
+      k_dots_df_few<12><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, live,
+                                                 self);
     else
       k_dots_df<<<grid, 256, sizeof(float4) * DFC, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip,
-                                                         self);
+                                                         live, self);
     k_reduce<<<dim3(nk + self, B), 256, 0, st>>>(part(), L.Gdf, ldp(), out, ldo, skip, 1);
     toc(ctx, T_ARNOLDI, st, 2);
     return cudaGetLastError();
@@ -688,11 +694,11 @@ struct Krylov {
     float4 *vout = Vdf() + (int64_t)nk * L.n;
     if (norm_out) {
       k_update_df<true><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, sc, base, vin(), L.n, vout,
-                                                      L.n, part(), ldp(), skip);
+                                                      L.n, part(), ldp(), skip, live);
       k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4, skip, 2);
     } else {
       k_update_df<false><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, sc, base, vin(), L.n, vout,
-                                                       L.n, nullptr, 0, skip);
+                                                       L.n, nullptr, 0, skip, live);
     }
     toc(ctx, T_ARNOLDI, st, norm_out ? 2 : 1);
     return cudaGetLastError();
@@ -737,6 +743,7 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
   d.stat = K.at<double>(K.L.off_stat);
   d.live = K.at<int>(K.L.off_live);
   d.sc = K.at<double>(K.L.off_sc);
+  K.live = d.live;
   d.kcnt = d.live + B;
   int *skip = d.live + 2 * B;
   const bool sel = o->reorth == 1;
