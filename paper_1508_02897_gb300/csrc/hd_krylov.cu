@@ -320,18 +320,28 @@ __global__ void __launch_bounds__(256) k_dots_df_few(const float4 *__restrict__ 
   }
 }
 
-// y_r = base_r - sum_k V_r[k] coef_r[k] sc_r[k]^2 (double-single accumulation): the stored
-// basis vectors are u_k = v_k / sc_k (normalised lazily, see k_arnoldi_step), so the
-// projection on v_k takes coef sc_k^2.  y_r goes to the basis slot vout_r as float pairs
-// and to y_r in FP64 (the preconditioner's input); optionally normpart[r][blk] = block
-// sum of |y_r|^2.
+// Scale of the first Gram-Schmidt pass's output in the double-single mode: 1 / ||w|| from
+// the pass's self dot product ||w||^2 (1 when that is zero or not finite).  The stored
+// vector then has the norm ||w - V h|| / ||w|| <= 1 whatever the norms of earlier ones, so
+// lazily normalised magnitudes cannot compound over a restart cycle.
+__host__ __device__ __forceinline__ double lazy_gamma(double w2) {
+  return (w2 > 0.0 && w2 < 1.0e300) ? 1.0 / sqrt(w2) : 1.0;
+}
+
+// y_r = g_r (base_r - sum_k V_r[k] coef_r[k] sc_r[k]^2) (double-single accumulation): the
+// stored basis vectors are u_k = v_k / sc_k (normalised lazily, see k_arnoldi_step), so
+// the projection on v_k takes coef sc_k^2.  With `scale`, g_r = lazy_gamma(coef_r[nk]) =
+// 1 / ||base_r|| from the first pass's self dot product, else 1.  y_r goes to the basis
+// slot vout_r as float pairs and to y_r in FP64 (the preconditioner's input); optionally
+// normpart[r][blk] = block sum of |y_r|^2.
 template <bool NORM>
 __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
                                                   const double2 *__restrict__ coef_all, int ldc,
                                                   const double *__restrict__ sc_all, const double2 *base_all,
                                                   double2 *y_all, int64_t ldy, float4 *__restrict__ vout_all,
                                                   int64_t n, double2 *__restrict__ normpart_all, int64_t ldp,
-                                                  const int *__restrict__ skip, const int *__restrict__ live) {
+                                                  const int *__restrict__ skip, const int *__restrict__ live,
+                                                  int scale) {
   extern __shared__ float4 csm[];  // [nk]
   __shared__ double nsm[DT / 32];
   const int tid = threadIdx.x, r = blockIdx.y;
@@ -342,9 +352,10 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
   const double2 *base = base_all + (int64_t)r * ldy;
   double2 *y = y_all + (int64_t)r * ldy;
   float4 *vout = vout_all + (int64_t)r * ldvr;
+  const double g = scale ? lazy_gamma(coef[nk].x) : 1.0;
   for (int k = tid; k < nk; k += DT) {
     const double2 c0 = coef[k];
-    const double s2 = sc[k] * sc[k];
+    const double s2 = sc[k] * sc[k] * g;
     const double2 c = make_double2(c0.x * s2, c0.y * s2);
     float2 cr = ds_split(c.x), ci = ds_split(c.y);
     csm[k] = make_float4(cr.x, cr.y, ci.x, ci.y);
@@ -386,7 +397,7 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
       if (i < n) {
         // y = base - acc in double-single, then one FP64 add per component
         const double2 bv = base[i];
-        const float2 br = ds_split(bv.x), bi = ds_split(bv.y);
+        const float2 br = ds_split(g * bv.x), bi = ds_split(g * bv.y);
         float oh = br.x, ol = br.y, qh = bi.x, ql = bi.y;
         ds_add(oh, ol, -rh[e], -rl[e]);
         ds_add(qh, ql, -ih[e], -il[e]);
@@ -467,7 +478,12 @@ __device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, a.y); }
 __global__ void k_reorth_decide(GmresDev d, int nk, int *skip) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= d.nrhs) return;
-  const double w2 = d.h1[(int64_t)r * d.ldh + nk].x, w1 = d.red[4 * r].x;
+  const double w2 = d.h1[(int64_t)r * d.ldh + nk].x;
+  double w1 = d.red[4 * r].x;
+  if (d.lazy) {   // the first pass wrote g (w - V h), g = lazy_gamma(||w||^2)
+    const double g = lazy_gamma(w2);
+    w1 /= g * g;
+  }
   skip[r] = (w1 >= 0.01 * w2) ? 1 : 0;
   d.stat[4 * r + 3] = (w1 >= 0.01 * w2) ? 0.0 : 1.0;   // second pass taken in this step
 }
@@ -486,9 +502,11 @@ __global__ void k_cycle_init(GmresDev d) {
 
 // Column j of H from the two CGS passes, old rotations, new rotation, g update.
 // Lazy normalisation (double-single mode): the stored vectors are u_k = v_k / sc_k and
-// the preconditioner ran on u_j, so w = A M u_j = (A z_j) / sc_j, the passes returned
-// u_k^H w, and the vector left over is y = (A z_j - sum_k h_kj v_k) / sc_j; hence
-// h_kj = sc_j sc_k (h1_k + h2_k), h_{j+1,j} = sc_j ||y|| and sc_{j+1} = 1 / ||y||.
+// the preconditioner ran on u_j, so w = A M u_j = (A z_j) / sc_j; the first pass returned
+// h1_k = u_k^H w and stored g (w - sum_k sc_k^2 h1_k u_k) with g = lazy_gamma(||w||^2),
+// the second (if any) h2_k = u_k^H of that and stored y = g (A z_j - sum_k h_kj v_k) / sc_j;
+// hence h_kj = sc_j sc_k (h1_k + h2_k / g), h_{j+1,j} = sc_j ||y|| / g and
+// sc_{j+1} = 1 / ||y||.
 __global__ void k_arnoldi_step(GmresDev d, int j) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= d.nrhs || !d.live[r]) return;
@@ -504,14 +522,14 @@ __global__ void k_arnoldi_step(GmresDev d, int j) {
   double hn = sqrt(d.red[4 * r].x);
   if (d.lazy) {
     double *sc = d.sc + (int64_t)r * d.ldh;
-    const double sj = sc[j];
+    const double sj = sc[j], g = lazy_gamma(h1[j + 1].x);
     for (int i = 0; i <= j; ++i) {
-      const double2 h = cadd(h1[i], h2[i]);
+      const double2 h = make_double2(h1[i].x + h2[i].x / g, h1[i].y + h2[i].y / g);
       const double f = sj * sc[i];
       Hj[i] = make_double2(f * h.x, f * h.y);
     }
     sc[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-    hn *= sj;
+    hn *= sj / g;
   } else {
     for (int i = 0; i <= j; ++i) Hj[i] = cadd(h1[i], h2[i]);
   }
@@ -688,17 +706,17 @@ struct Krylov {
   }
   // y = base - V (coef sc^2) into vin (FP64) and into basis slot nk (float pairs)
   cudaError_t update_df(int nk, const double2 *coef, int ldc, const double *sc, const double2 *base,
-                        double2 *norm_out, const int *skip = nullptr) {
+                        double2 *norm_out, int scale, const int *skip = nullptr) {
     tic(ctx, T_ARNOLDI, st);
     size_t sm = sizeof(float4) * nk;
     float4 *vout = Vdf() + (int64_t)nk * L.n;
     if (norm_out) {
       k_update_df<true><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, sc, base, vin(), L.n, vout,
-                                                      L.n, part(), ldp(), skip, live);
+                                                      L.n, part(), ldp(), skip, live, scale);
       k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4, skip, 2);
     } else {
       k_update_df<false><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, sc, base, vin(), L.n, vout,
-                                                       L.n, nullptr, 0, skip, live);
+                                                       L.n, nullptr, 0, skip, live, scale);
     }
     toc(ctx, T_ARNOLDI, st, norm_out ? 2 : 1);
     return cudaGetLastError();
@@ -827,7 +845,7 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
       // CGS2: h1 = V^H w, w -= V h1, h2 = V^H w, w -= V h2; with selective
       // reorthogonalisation the second pass is skipped (h2 = 0) unless the first
       // cancelled more than a factor 10 of ||w||.
-      const int self = sel ? 1 : 0;
+      const int self = (sel || dsm) ? 1 : 0;   // ||w||^2: the selective rule, the lazy scale
       tic(ctx, T_MATVEC, st);
       KCHK(launch_matvec(ctx, zj, zs, K.w(), n, B, st));
       toc(ctx, T_MATVEC, st, 1);
@@ -835,10 +853,10 @@ static int run_gmres_batch_on(hd_ctx *ctx, const double2 *b, double2 *x, int B, 
         // the vector left after each pass goes straight to vin and basis slot j + 1,
         // unnormalised (k_arnoldi_step records its scale)
         KCHK(K.dots_df(j + 1, K.w(), d.h1, R + 1, nullptr, self));
-        KCHK(K.update_df(j + 1, d.h1, R + 1, d.sc, K.w(), sel ? d.red : nullptr));
+        KCHK(K.update_df(j + 1, d.h1, R + 1, d.sc, K.w(), sel ? d.red : nullptr, 1));
         if (sel) k_reorth_decide<<<nb, tb, 0, st>>>(d, j + 1, skip);
         KCHK(K.dots_df(j + 1, K.vin(), d.h2, R + 1, sel ? skip : nullptr));
-        KCHK(K.update_df(j + 1, d.h2, R + 1, d.sc, K.vin(), d.red, sel ? skip : nullptr));
+        KCHK(K.update_df(j + 1, d.h2, R + 1, d.sc, K.vin(), d.red, 0, sel ? skip : nullptr));
       } else {
         KCHK(K.dots(K.V(), K.ldvr(), j + 1, K.w(), d.h1, R + 1, nullptr, self));
         KCHK(K.update(K.V(), K.ldvr(), j + 1, nullptr, d.h1, R + 1, -1.0, K.w(), K.w(), sel ? d.red : nullptr));
