@@ -126,7 +126,8 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *decomp, 
  *   scratch_bytes : per-box staging of the local substitutions for nrhs
  *                   right-hand sides (apply) or the per-box working matrix
  *                   (factorisation), whichever is larger
- * Any output pointer may be NULL. */
+ * Any output pointer may be NULL.  nrhs >= 1 and 1 <= restart <= HD_MAX_RESTART,
+ * else HD_ERR_INVALID. */
 int hd_query_workspace(const hd_ctx *ctx, int32_t nrhs, int32_t restart, size_t *factor_bytes,
                        size_t *krylov_bytes, size_t *scratch_bytes);
 
@@ -205,8 +206,13 @@ typedef enum {
  * hd_apply_precond; right-hand sides are processed in groups that fit the array. */
 int hd_apply_precond_noalloc(hd_ctx *ctx, const void *r_dev, void *z_dev, int32_t nrhs, void *stream);
 
+/* Largest FGMRES restart length (Krylov vectors per cycle) the solver takes; the
+ * per-step Gram-Schmidt kernels keep one coefficient per basis vector in shared
+ * memory. */
+#define HD_MAX_RESTART 256
+
 typedef struct {
-  int32_t restart;    /* Krylov vectors per cycle                                  */
+  int32_t restart;    /* Krylov vectors per cycle, 1 .. HD_MAX_RESTART              */
   int32_t max_iters;  /* Arnoldi steps over all cycles                             */
   double rtol;        /* stop when ||b - A x|| <= rtol ||b||                        */
   int32_t use_x0;     /* 1: start from x_dev, 0: x0 = 0                              */

@@ -21,6 +21,7 @@ HD_SYMMETRIC = 0x100
 HD_TCORE = 0x200
 HD_SMOOTH = 0x400
 HD_ARNOLDI_FP64, HD_ARNOLDI_DS = 0, 1
+HD_MAX_RESTART = 256
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID", 2: "HD_ERR_OOM", 3: "HD_ERR_CUDA", 4: "HD_ERR_NOT_CONVERGED",
                 5: "HD_ERR_NUMERIC", 6: "HD_ERR_TIMEOUT", 7: "HD_PENDING"}
 TIMER_CLASSES = ("factor", "subst", "gather", "matvec", "arnoldi", "other")

@@ -249,8 +249,9 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
 
 int hd_query_workspace(const hd_ctx *c, int32_t nrhs, int32_t restart, size_t *factor_bytes, size_t *krylov_bytes_out,
                        size_t *scratch_bytes) {
+  if (nrhs < 1 || restart < 1 || restart > HD_MAX_RESTART)
+    return invalid("hd_query_workspace: nrhs must be >= 1 and restart in 1 .. HD_MAX_RESTART");
   if (!c) return invalid("hd_query_workspace: NULL context");
-  if (nrhs < 1 || restart < 1) return invalid("hd_query_workspace: nrhs and restart must be >= 1");
   const size_t cs = compute_bytes(c->prec);
   if (factor_bytes) *factor_bytes = store_bytes(c->prec) * (size_t)c->factor_elems;
   if (scratch_bytes) *scratch_bytes = cs * (size_t)std::max(c->staging_elems * (int64_t)nrhs, c->work_elems);
@@ -342,11 +343,13 @@ int hd_apply_ddm(hd_ctx *c, const void *f, void *u, int32_t nrhs, int32_t nsteps
 
 int hd_gmres_solve(hd_ctx *c, const void *b, void *x, int32_t nrhs, const hd_gmres_opts *o, void *kws, size_t kbytes,
                    void *scratch, size_t scratch_bytes, hd_gmres_stats *stats, void *stream) {
-  if (!c || !b || !x || !o || !kws || !scratch || !stats || nrhs < 1) return invalid("hd_gmres_solve: bad argument");
-  if (!c->factored) return invalid("hd_gmres_solve: call hd_factor_subdomains first");
-  if (o->restart < 1 || o->max_iters < 0 || !(o->rtol >= 0) || (o->arnoldi != HD_ARNOLDI_FP64 && o->arnoldi != HD_ARNOLDI_DS) ||
-      (o->reorth != 0 && o->reorth != 1) || o->precond_steps < 0 || o->precond_steps > 64)
+  if (!o) return invalid("hd_gmres_solve: bad argument");
+  if (o->restart < 1 || o->restart > HD_MAX_RESTART || o->max_iters < 0 || !(o->rtol >= 0) ||
+      (o->arnoldi != HD_ARNOLDI_FP64 && o->arnoldi != HD_ARNOLDI_DS) || (o->reorth != 0 && o->reorth != 1) ||
+      o->precond_steps < 0 || o->precond_steps > 64)
     return invalid("hd_gmres_solve: bad options");
+  if (!c || !b || !x || !kws || !scratch || !stats || nrhs < 1) return invalid("hd_gmres_solve: bad argument");
+  if (!c->factored) return invalid("hd_gmres_solve: call hd_factor_subdomains first");
   size_t kb, sb;
   hd_query_workspace(c, nrhs, o->restart, nullptr, &kb, &sb);
   if (kbytes < kb) { set_error("hd_gmres_solve: krylov workspace too small for nrhs right-hand sides"); return HD_ERR_OOM; }

@@ -51,3 +51,20 @@ def test_storage_flags_and_new_entry_points_validate_without_gpu():
     o = B.hd_gmres_opts(10, 100, 1e-6, 0, B.HD_ARNOLDI_DS, 0, 1, 1)
     st = (B.hd_gmres_stats * 1)()
     assert L.hd_gmres_solve(None, p, p, 1, ctypes.byref(o), p, 1 << 20, p, 1 << 20, st, None) == B.HD_ERR_INVALID
+
+
+def test_restart_bound_is_enforced_without_gpu():
+    """restart beyond HD_MAX_RESTART is refused by the workspace query, the solver and
+    the server before any pointer is used or any CUDA call is made."""
+    from paper_1508_02897_gb300 import _binding as B
+    L = B.lib()
+    for restart in (0, B.HD_MAX_RESTART + 1):
+        with pytest.raises(B.HDError) as e:
+            B.hd_query_workspace(None, 1, restart)
+        assert e.value.code == B.HD_ERR_INVALID and "restart" in B.hd_last_error()
+        p = ctypes.c_void_p(16)   # never dereferenced: validation fails first
+        o = B.hd_gmres_opts(restart, 100, 1e-6, 0, B.HD_ARNOLDI_DS, 0, 1, 1)
+        st = (B.hd_gmres_stats * 1)()
+        assert L.hd_gmres_solve(p, p, p, 1, ctypes.byref(o), p, 1 << 20, p, 1 << 20, st, None) == B.HD_ERR_INVALID
+        assert "bad options" in B.hd_last_error()
+
