@@ -136,6 +136,8 @@ class HelmholtzDDM:
         b, nrhs = self._vec(b)
         if out is not None:
             x = out
+            if x0 is not None:   # the solver starts from the contents of x
+                x.copy_(self._vec(x0)[0].view_as(x))
         elif x0 is not None:
             x = self._vec(x0)[0].clone()
         else:

@@ -61,3 +61,30 @@ def test_arnoldi_step_indices_follow_the_cycles():
     assert bench._arnoldi_js(0, 10) == []
     assert bench._arnoldi_js(3, 10) == [0, 1, 2]
     assert bench._arnoldi_js(23, 10) == list(range(10)) * 2 + [0, 1, 2]
+
+
+def test_solve_starts_from_x0_when_out_is_given(monkeypatch):
+    """HelmholtzDDM.solve hands the C ABI the initial guess in the output buffer: with
+    both out and x0 the buffer must hold x0 (host logic only: the ABI call is stubbed)."""
+    import torch
+    from paper_1508_02897_gb300 import solver as S
+    seen = {}
+
+    def fake_solve(ctx, b_ptr, x_ptr, nrhs, *args, **kw):
+        seen["use_x0"] = kw["use_x0"]
+        return 0, []
+
+    monkeypatch.setattr(S.B, "hd_gmres_solve", fake_solve)
+    monkeypatch.setattr(S, "_stream_ptr", lambda stream: 0)
+    s = S.HelmholtzDDM.__new__(S.HelmholtzDDM)
+    s.n, s.device, s.stream, s.prec, s.ctx = 4, torch.device("cpu"), None, S.B.HD_C64, None
+    s.scratch, s.scratch_bytes = torch.empty(16, dtype=torch.uint8), 16
+    s._krylov = {(5, 1): torch.empty(16, dtype=torch.uint8)}
+    b = torch.ones((4, 4), dtype=torch.complex128)
+    x0 = torch.full((4, 4), 2 + 1j, dtype=torch.complex128)
+    out = torch.zeros((4, 4), dtype=torch.complex128)
+    x, _ = s.solve(b, restart=5, x0=x0, out=out)
+    assert x is out and torch.equal(out, x0) and seen["use_x0"] == 1
+    x, _ = s.solve(b, restart=5, out=torch.zeros((4, 4), dtype=torch.complex128))
+    assert seen["use_x0"] == 0
+
