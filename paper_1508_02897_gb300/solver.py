@@ -54,8 +54,11 @@ class HelmholtzDDM:
                                      pml_power)
         fb, _, sb = B.hd_query_workspace(self.ctx, 1, 1)
         self.factor_bytes, self.scratch_bytes = fb, sb
-        self.factor_buf = torch.empty(max(fb, 16), dtype=torch.uint8, device=self.device)
-        self.scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device=self.device)
+        # workspaces are allocated on the stream the kernels run on, so the caching
+        # allocator never hands a replaced buffer out while queued kernels still use it
+        with torch.cuda.stream(self.stream):
+            self.factor_buf = torch.empty(max(fb, 16), dtype=torch.uint8, device=self.device)
+            self.scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device=self.device)
         self._krylov = {}
         self.factored = False
         if factor:
@@ -106,11 +109,12 @@ class HelmholtzDDM:
         solves, each round's sources the neighbours' residuals on the owned boxes."""
         f, nrhs = self._vec(f)
         u = torch.empty_like(f) if out is None else out
-        work = torch.empty(2 * f.numel() * 16, dtype=torch.uint8, device=self.device)
         _, _, sb = B.hd_query_workspace(self.ctx, nrhs, 1)
-        if sb > self.scratch_bytes:
-            self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
-            self.scratch_bytes = sb
+        with torch.cuda.stream(self.stream):
+            work = torch.empty(2 * f.numel() * 16, dtype=torch.uint8, device=self.device)
+            if sb > self.scratch_bytes:
+                self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+                self.scratch_bytes = sb
         B.hd_apply_ddm(self.ctx, f.data_ptr(), u.data_ptr(), nrhs, steps, work.data_ptr(), work.numel(),
                        self.scratch.data_ptr(), self.scratch_bytes, self._st())
         return u
@@ -120,10 +124,11 @@ class HelmholtzDDM:
         if key not in self._krylov:
             _, kb, sb = B.hd_query_workspace(self.ctx, nrhs, restart)
             self._krylov.clear()
-            self._krylov[key] = torch.empty(kb, dtype=torch.uint8, device=self.device)
-            if sb > self.scratch_bytes:
-                self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
-                self.scratch_bytes = sb
+            with torch.cuda.stream(self.stream):
+                self._krylov[key] = torch.empty(kb, dtype=torch.uint8, device=self.device)
+                if sb > self.scratch_bytes:
+                    self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+                    self.scratch_bytes = sb
         return self._krylov[key]
 
     def solve(self, b, restart: int = 50, rtol: float = 1e-8, max_iters: int = 1000, x0=None, out=None,
