@@ -218,7 +218,7 @@ typedef struct {
   int32_t use_x0;     /* 1: start from x_dev, 0: x0 = 0                              */
   int32_t arnoldi;    /* hd_arnoldi_mode                                            */
   int32_t graphs;     /* 1: capture each Arnoldi step j (preconditioner, matvec, CGS2,
-                         Givens, scaling) once as a CUDA graph per workspace and
+                         Givens, normalisation) once as a CUDA graph per workspace and
                          replay it in later cycles and solves; 0: plain launches   */
   int32_t reorth;     /* 0: always two Gram-Schmidt passes (CGS2); 1: second pass only
                          when the first cancelled more than a factor 10 of ||w||

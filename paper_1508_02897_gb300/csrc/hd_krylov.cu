@@ -425,7 +425,8 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
   }
 }
 
-// v_r = w_r * red[4 r + 1].x written twice: split into V (double-single) and FP64 into vin.
+// v_r = w_r * red[4 r + 1].x written twice: split into V (double-single) and FP64 into vin
+// (the normalised first vector of each restart cycle; later ones are stored lazily).
 // SCE elements per thread with all loads issued first (one element per thread left too
 // few bytes in flight: 2.6 TB/s at 4096^2).
 constexpr int SCE = 4;
