@@ -7,4 +7,5 @@ only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 from .helmholtz import (  # noqa: F401
     Grid, Subdomain, pml_profile, helmholtz_matrix, global_operator, rhs_from_source,
     decompose, local_operator, DDMPreconditioner, fgmres, FGMRESResult, smoothstep5, smoothing_profile,
+    block_fgmres, BlockFGMRESResult,
 )

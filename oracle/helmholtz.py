@@ -399,3 +399,79 @@ def fgmres(apply_A: Callable[[np.ndarray], np.ndarray], apply_M: Callable[[np.nd
             y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
         x = x + Z[:k].T @ y
         cycles += 1
+
+
+@dataclass
+class BlockFGMRESResult:
+    x: np.ndarray                 # [p, n]
+    iters: int                    # block Arnoldi steps over all cycles
+    restarts: int
+    converged: np.ndarray         # [p] bool
+    relres_est: np.ndarray        # [p]
+    relres_true: np.ndarray       # [p]
+    history: List[np.ndarray] = field(default_factory=list)
+
+
+def block_fgmres(apply_A: Callable[[np.ndarray], np.ndarray], apply_M: Callable[[np.ndarray], np.ndarray],
+                 B: np.ndarray, restart: int, rtol: float, max_iters: int) -> BlockFGMRESResult:
+    """Restarted right-preconditioned block flexible GMRES for A X = B with p
+    right-hand sides sharing one Krylov space (the outer solver of Sec. 3 taken to many
+    sources at once; the block method itself is the textbook one, e.g. Saad, *Iterative
+    Methods for Sparse Linear Systems*, 2nd ed., Sec. 6.12, made flexible as in Sec. 9.4).
+
+    Per cycle: R = B - A X and R = V_0 S (thin QR, V_0 n x p); block Arnoldi step j:
+    Z_j = M V_j (M applied to every column), W = A Z_j, H_ij = V_i^H W and W -= V_i H_ij for
+    i <= j, applied twice (classical Gram-Schmidt), W = V_{j+1} H_{j+1,j} (thin QR); Y
+    minimises || E_1 S - Hbar_j Y ||_F (least squares) and the column norms of that
+    residual are the columns' residual estimates.  The cycle ends when every column's
+    estimate is <= rtol ||b_c|| (or at the restart, or when a new block is rank
+    deficient); then X += [Z_0 .. Z_j] Y and the true residual decides whether to restart.
+    x0 = 0.  ``iters`` counts block Arnoldi steps.
+    """
+    B = np.asarray(B, dtype=np.complex128)
+    p = B.shape[0]
+    Bm = B.reshape(p, -1).T                                  # n x p, columns are right-hand sides
+    n = Bm.shape[0]
+    bnorm = np.linalg.norm(Bm, axis=0)
+    X = np.zeros_like(Bm)
+    iters, cycles, history = 0, 0, []
+    est = np.ones(p)
+    A_cols = lambda M_: np.stack([apply_A(M_[:, c]) for c in range(M_.shape[1])], axis=1)
+    M_cols = lambda M_: np.stack([np.asarray(apply_M(M_[:, c])).ravel() for c in range(M_.shape[1])], axis=1)
+    while True:
+        R = Bm - A_cols(X) if cycles > 0 else Bm.copy()
+        true = np.linalg.norm(R, axis=0) / np.where(bnorm > 0, bnorm, 1.0)
+        if np.all(true <= rtol) or iters >= max_iters:
+            return BlockFGMRESResult(X.T.reshape(B.shape), iters, cycles, true <= rtol, est, true, history)
+        V0, S = np.linalg.qr(R)
+        V, Z = [V0], []
+        Hbar = np.zeros(((restart + 1) * p, restart * p), dtype=np.complex128)
+        E1S = np.zeros(((restart + 1) * p, p), dtype=np.complex128)
+        E1S[:p] = S
+        k = 0
+        Y = np.zeros((0, p), dtype=np.complex128)
+        for j in range(restart):
+            Z.append(M_cols(V[j]))
+            W = A_cols(Z[j])
+            wnorm = np.linalg.norm(W)
+            for _ in range(2):
+                for i in range(j + 1):
+                    Hij = V[i].conj().T @ W
+                    W = W - V[i] @ Hij
+                    Hbar[i * p:(i + 1) * p, j * p:(j + 1) * p] += Hij
+            Vn, Hn = np.linalg.qr(W)
+            Hbar[(j + 1) * p:(j + 2) * p, j * p:(j + 1) * p] = Hn
+            V.append(Vn)
+            iters += 1
+            k = j + 1
+            rows, cols = (k + 1) * p, k * p
+            Y = np.linalg.lstsq(Hbar[:rows, :cols], E1S[:rows], rcond=None)[0]
+            est = np.linalg.norm(E1S[:rows] - Hbar[:rows, :cols] @ Y, axis=0) / np.where(bnorm > 0, bnorm, 1.0)
+            history.append(est.copy())
+            # a direction of the new block that Gram-Schmidt cancelled to rounding level: the
+            # block Krylov space stops growing there (no deflation: the cycle ends)
+            deficient = np.min(np.abs(np.diag(Hn))) <= 1e-12 * max(wnorm, 1e-300)
+            if np.all(est <= rtol) or deficient or iters >= max_iters:
+                break
+        X = X + np.concatenate(Z[:k], axis=1) @ Y
+        cycles += 1
