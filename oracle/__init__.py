@@ -6,6 +6,7 @@ only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 """
 from .helmholtz import (  # noqa: F401
     Grid, Subdomain, pml_profile, helmholtz_matrix, global_operator, rhs_from_source,
-    decompose, local_operator, DDMPreconditioner, fgmres, FGMRESResult, smoothstep5, smoothing_profile,
+    decompose, local_operator, factor_box, oracle_threads, DDMPreconditioner, fgmres, FGMRESResult, smoothstep5, smoothing_profile,
     block_fgmres, BlockFGMRESResult,
 )
+from .banded import BandLU, box_order, build_banded  # noqa: F401

@@ -31,17 +31,20 @@ garbled the reading used is stated in the docstring:
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 from dataclasses import dataclass, field
 from typing import Callable, List, Optional, Sequence
 
 import numpy as np
 import scipy.sparse as sp
-import scipy.sparse.linalg as spla
+
+from .banded import BandLU, box_order
 
 __all__ = [
     "Grid", "Subdomain", "pml_profile", "helmholtz_matrix", "global_operator", "rhs_from_source",
-    "decompose", "local_operator", "DDMPreconditioner", "fgmres", "FGMRESResult", "smoothstep5",
-    "smoothing_profile",
+    "decompose", "local_operator", "factor_box", "oracle_threads", "DDMPreconditioner", "fgmres", "FGMRESResult",
+    "smoothstep5", "smoothing_profile",
 ]
 
 
@@ -210,16 +213,31 @@ def smoothing_profile(o0: int, o1: int, e0: int, e1: int) -> np.ndarray:
     return b
 
 
+def factor_box(grid: Grid, k2: np.ndarray, s: Subdomain) -> BandLU:
+    """The local PML problem of Eq. (pmlij) on box s, factorised once with the
+    oracle's own banded LU with partial pivoting (Sec. 3: "factorized and solved
+    with direct solver"; the paper does not name it), unknowns ordered so that the
+    band is the shorter side of the box (bandwidth min(width, height))."""
+    return BandLU(local_operator(grid, k2, s), box_order(s.ex1 - s.ex0, s.ey1 - s.ey0))
+
+
+def oracle_threads() -> int:
+    """Threads that factorise boxes at once: HD_ORACLE_THREADS, else every host core."""
+    return max(1, int(os.environ.get("HD_ORACLE_THREADS", "0")) or (os.cpu_count() or 1))
+
+
 class DDMPreconditioner:
     """One-step preconditioner of Eq. (ddm0) and Eq. (pc): restrict the input to
     every owned box, solve every local PML problem, and add each full local
     solution (including its PML area) into the output.  No smoothing function
     (the Remark after Eq. (pc) omits it).  Each local problem is factorised once
-    with a sparse direct solver (Sec. 3: "factorized and solved with direct
-    solver"; the paper does not name it)."""
+    with the oracle's banded direct solver (``factor_box``); the boxes are
+    independent, so several factorise at once in threads (``threads``, default
+    ``oracle_threads()``); the result does not depend on the thread count."""
 
     def __init__(self, grid: Grid, c: np.ndarray, cut_x, cut_y, overlap: int,
-                 own_global_pml: bool = True, subdomains: Optional[Sequence[int]] = None, smoothing: bool = False):
+                 own_global_pml: bool = True, subdomains: Optional[Sequence[int]] = None, smoothing: bool = False,
+                 threads: Optional[int] = None):
         self.grid = grid
         self.smoothing = smoothing
         self.c = np.asarray(c, dtype=np.float64)
@@ -227,10 +245,10 @@ class DDMPreconditioner:
         self._A = None
         self.subs = decompose(grid, cut_x, cut_y, overlap, own_global_pml)
         self.active = list(range(len(self.subs))) if subdomains is None else list(subdomains)
-        self.lu = {}
-        for s_idx in self.active:
-            A = local_operator(grid, self.k2, self.subs[s_idx]).tocsc()
-            self.lu[s_idx] = spla.splu(A)
+        nthr = min(threads or oracle_threads(), max(1, len(self.active)))
+        with ThreadPoolExecutor(max_workers=nthr) as ex:
+            lus = list(ex.map(lambda t: factor_box(grid, self.k2, self.subs[t]), self.active))
+        self.lu = dict(zip(self.active, lus))
 
     def local_solve(self, s_idx: int, r: np.ndarray) -> np.ndarray:
         """u_ij^0 of Eq. (ddm0): local solve with r restricted to the owned box."""
