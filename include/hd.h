@@ -135,13 +135,45 @@ int hd_query_workspace(const hd_ctx *ctx, int32_t nrhs, int32_t restart, size_t 
  * solved with direct solver") as a block-tridiagonal LU along the grid rows of
  * the box: S_0 = D_0, S_j = D_j - L_j S_{j-1}^{-1} U_{j-1} (L_j, U_j diagonal,
  * D_j tridiagonal), storing every S_j^{-1} (m x m, m = box width, column-major)
- * in factor_dev.  Each S_j is inverted by Gauss-Jordan elimination with
- * partial pivoting.  factor_dev stays bound to the context (the caller keeps
- * it alive until hd_destroy or the next factorisation).  scratch_dev is free
- * again when the call's work on `stream` ends.  Returns HD_ERR_NUMERIC later
- * (from hd_gmres_solve / hd_check_status) if a pivot was zero. */
+ * in factor_dev.  Each S_j is inverted by Gauss-Jordan elimination.  With
+ * complex FP32 arithmetic (HD_C64, HD_C64_H) and boxes at most 192 wide the
+ * default kernel keeps S_j in tensor memory and eliminates it without pivoting,
+ * 16 columns per step, each step one rank-16 complex update on the tensor cores
+ * (tcgen05 MMAs on operands split into three BF16 pieces, FP32 accumulation);
+ * it checks every pivot, and a box with a pivot below pivot_ratio times the
+ * largest unprocessed entry of its column (hd_set_factor_path) is factorised
+ * again by the SIMT kernel with partial pivoting, in the same call.  Otherwise
+ * (HD_C128, wider boxes, or HD_FACTOR_SIMT) the SIMT kernel with partial
+ * pivoting factorises every box.  factor_dev stays bound to the context (the
+ * caller keeps it alive until hd_destroy or the next factorisation).
+ * scratch_dev is free again when the call's work on `stream` ends.  Returns
+ * HD_ERR_NUMERIC later (from hd_gmres_solve / hd_check_status) if a pivot was
+ * zero. */
 int hd_factor_subdomains(hd_ctx *ctx, void *factor_dev, size_t factor_bytes, void *scratch_dev,
                          size_t scratch_bytes, void *stream);
+
+/* Kernel choice of hd_factor_subdomains (no counterpart in the paper, which names
+ * no direct solver). */
+typedef enum {
+  HD_FACTOR_AUTO = 0,   /* tensor cores where they apply, else the SIMT kernel          */
+  HD_FACTOR_SIMT = 1,   /* Gauss-Jordan with partial pivoting on the CUDA cores         */
+  HD_FACTOR_TCORE = 2   /* tensor cores; hd_factor_subdomains fails with HD_ERR_INVALID
+                           where they do not apply                                     */
+} hd_factor_path;
+
+/* Selects the factorisation kernel for later hd_factor_subdomains calls on ctx and
+ * the pivot check of the tensor-core kernel: a box is refactorised with partial
+ * pivoting when some pivot p has |p| < pivot_ratio * max |entry| over the other
+ * unprocessed rows checked in its column (0 < pivot_ratio; the default 0.5 lets
+ * multipliers reach at most 2).  HD_ERR_INVALID for an unknown path or a
+ * non-positive or non-finite ratio. */
+int hd_set_factor_path(hd_ctx *ctx, int32_t path, double pivot_ratio);
+
+/* How the last hd_factor_subdomains on ctx factorised its boxes: *tcore_boxes
+ * kept the tensor-core result, *pivoted_boxes were (re)factorised with partial
+ * pivoting.  Synchronises `stream`.  Outputs may be NULL; HD_ERR_INVALID before
+ * any factorisation. */
+int hd_factor_report(hd_ctx *ctx, int32_t *tcore_boxes, int32_t *pivoted_boxes, void *stream);
 
 /* y = A x for nrhs vectors: A is the PML operator of Eq. (pml) multiplied by
  * J h^2 (J = alpha1 alpha2), a complex-symmetric 5-point matrix with

@@ -21,6 +21,7 @@ HD_SYMMETRIC = 0x100
 HD_TCORE = 0x200
 HD_SMOOTH = 0x400
 HD_ARNOLDI_FP64, HD_ARNOLDI_DS = 0, 1
+HD_FACTOR_AUTO, HD_FACTOR_SIMT, HD_FACTOR_TCORE = 0, 1, 2
 HD_MAX_RESTART = 256
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID", 2: "HD_ERR_OOM", 3: "HD_ERR_CUDA", 4: "HD_ERR_NOT_CONVERGED",
                 5: "HD_ERR_NUMERIC", 6: "HD_ERR_TIMEOUT", 7: "HD_PENDING"}
@@ -82,6 +83,8 @@ _SIGS = {
     "hd_query_workspace": [_P, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t),
                            ct.POINTER(ct.c_size_t)],
     "hd_factor_subdomains": [_P, _P, ct.c_size_t, _P, ct.c_size_t, _P],
+    "hd_set_factor_path": [_P, ct.c_int32, ct.c_double],
+    "hd_factor_report": [_P, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32), _P],
     "hd_matvec": [_P, _P, _P, ct.c_int32, _P],
     "hd_rhs_from_source": [_P, _P, _P, ct.c_int32, _P],
     "hd_apply_precond": [_P, _P, _P, ct.c_int32, _P, ct.c_size_t, _P],
@@ -164,6 +167,17 @@ def hd_query_workspace(ctx, nrhs, restart):
 
 def hd_factor_subdomains(ctx, factor_ptr, factor_bytes, scratch_ptr, scratch_bytes, stream):
     _check("hd_factor_subdomains", lib().hd_factor_subdomains(ctx, factor_ptr, factor_bytes, scratch_ptr, scratch_bytes, stream))
+
+
+def hd_set_factor_path(ctx, path, pivot_ratio=0.5):
+    _check("hd_set_factor_path", lib().hd_set_factor_path(ctx, int(path), float(pivot_ratio)))
+
+
+def hd_factor_report(ctx, stream):
+    """(boxes kept from the tensor-core factorisation, boxes factorised with partial pivoting)."""
+    t, p = ct.c_int32(), ct.c_int32()
+    _check("hd_factor_report", lib().hd_factor_report(ctx, ct.byref(t), ct.byref(p), stream))
+    return t.value, p.value
 
 
 def hd_matvec(ctx, x_ptr, y_ptr, nrhs, stream):

@@ -91,6 +91,7 @@ static void free_ctx(hd_ctx *c) {
   if (c->d_nearx) cudaFreeAsync(c->d_nearx, c->stream);
   if (c->d_neary) cudaFreeAsync(c->d_neary, c->stream);
   if (c->d_status) cudaFreeAsync(c->d_status, c->stream);
+  if (c->d_fflag) cudaFreeAsync(c->d_fflag, c->stream);
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   delete c;
 }
@@ -221,6 +222,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   ALLOC(c->d_nearx, sizeof(int32_t) * c->NX);
   ALLOC(c->d_neary, sizeof(int32_t) * c->NY);
   ALLOC(c->d_status, sizeof(int32_t));
+  ALLOC(c->d_fflag, sizeof(int32_t) * c->nsub);
 #undef ALLOC
   cudaError_t e;
 #define CP(dst, src, bytes)                                                                        \
@@ -235,6 +237,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   CP(c->d_neary, neary.data(), sizeof(int32_t) * c->NY);
 #undef CP
   e = cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_fflag, 0, sizeof(int32_t) * c->nsub, st);
   if (e == cudaSuccess) e = launch_setup_tables(c, c_dev, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "hd_setup_medium"); }
@@ -274,6 +277,35 @@ int hd_factor_subdomains(hd_ctx *c, void *factor, size_t factor_bytes, void *scr
   if (rc) return rc;
   c->factor = factor;
   c->factored = true;
+  return HD_OK;
+}
+
+int hd_set_factor_path(hd_ctx *c, int32_t path, double pivot_ratio) {
+  if (!c) return invalid("hd_set_factor_path: NULL context");
+  if (path != HD_FACTOR_AUTO && path != HD_FACTOR_SIMT && path != HD_FACTOR_TCORE)
+    return invalid("hd_set_factor_path: unknown path");
+  if (!(pivot_ratio > 0) || !std::isfinite(pivot_ratio)) return invalid("hd_set_factor_path: pivot_ratio must be > 0");
+  c->fpath = path;
+  c->fpivot = pivot_ratio;
+  return HD_OK;
+}
+
+int hd_factor_report(hd_ctx *c, int32_t *tcore_boxes, int32_t *pivoted_boxes, void *stream) {
+  if (!c) return invalid("hd_factor_report: NULL context");
+  if (c->last_fpath < 0) return invalid("hd_factor_report: no factorisation yet");
+  int32_t tcb = 0, piv = c->nsub;
+  if (c->last_fpath == HD_FACTOR_TCORE) {
+    std::vector<int32_t> fl(c->nsub);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(fl.data(), c->d_fflag, sizeof(int32_t) * c->nsub, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "hd_factor_report");
+    piv = 0;
+    for (int32_t f : fl) piv += f != 0;
+    tcb = c->nsub - piv;
+  }
+  if (tcore_boxes) *tcore_boxes = tcb;
+  if (pivoted_boxes) *pivoted_boxes = piv;
   return HD_OK;
 }
 

@@ -57,31 +57,6 @@ size_t factor_smem_bytes(int prec, int max_m) {
 
 template <typename T> __device__ __forceinline__ auto cabs2(T a) { return a.x * a.x + a.y * a.y; }
 
-// Entries of D_j (tridiagonal) and the coupling L_j of grid row j, Eq. (pml)
-// discretised with the box's own PML tables.
-template <typename T, typename R>
-__device__ __forceinline__ T d_entry(int r, int c, int j, const double2 *a1c, const double2 *ia1f, const double2 *a2c,
-                                     const double2 *ia2f, const double *k2row, double h2) {
-  const double2 a2 = a2c[j];
-  if (r == c) {
-    const double2 a1 = a1c[r];
-    const double2 cw = cmul(a2, ia1f[r]), ce = cmul(a2, ia1f[r + 1]);
-    const double2 cs = cmul(a1, ia2f[j]), cn = cmul(a1, ia2f[j + 1]);
-    const double2 j12 = cmul(a1, a2);
-    const double hk = mul_rn(h2, k2row[r]);
-    return mk<T>((R)(-(cw.x + ce.x + cs.x + cn.x) + hk * j12.x), (R)(-(cw.y + ce.y + cs.y + cn.y) + hk * j12.y));
-  }
-  if (r == c + 1) {
-    const double2 cw = cmul(a2, ia1f[r]);      // row r couples to column r-1 (west)
-    return mk<T>((R)cw.x, (R)cw.y);
-  }
-  if (r + 1 == c) {
-    const double2 ce = cmul(a2, ia1f[r + 1]);  // row r couples to column r+1 (east)
-    return mk<T>((R)ce.x, (R)ce.y);
-  }
-  return mk<T>(0, 0);
-}
-
 // Block-wide argmax of v over the CTA (ties: smaller index); every thread gets the
 // result.  sv/si hold one entry per warp; callers alternate two such buffers so a
 // fast warp of the next call cannot overwrite what a slow warp still reads.
@@ -109,27 +84,11 @@ __device__ __forceinline__ void block_argmax(R v, int idx, R *sv, int *si, R &be
   bi = __shfl_sync(0xffffffffu, i2, 0);
 }
 
-// Storage layouts of the S_j^{-1}: full column-major blocks, upper 16 x 16 tiles,
-// or TF32 real/imaginary planes in the tensor-core operand layout (HD_TCORE).
-enum { LAY_FULL = 0, LAY_SYM = 1, LAY_TC = 2 };
-
-__device__ __forceinline__ float tf32_round(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// d_entry restricted to its tridiagonal band (zero elsewhere without touching the tables)
-template <typename T, typename R>
-__device__ __forceinline__ T d_band(int r, int c, int j, const double2 *a1c, const double2 *ia1f, const double2 *a2c,
-                                    const double2 *ia2f, const double *k2row, double h2) {
-  return (r - c <= 1 && c - r <= 1) ? d_entry<T, R>(r, c, j, a1c, ia1f, a2c, ia2f, k2row, h2) : mk<T>(0, 0);
-}
-
 template <typename R, typename S, int LAY>
 __global__ void __launch_bounds__(FT, factor_ctas<R>())
 k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, const double *__restrict__ k2, int NX,
-         double h2, S *__restrict__ factor, C<R> *__restrict__ work, int32_t *status) {
+         double h2, S *__restrict__ factor, C<R> *__restrict__ work, int32_t *status, const int32_t *only) {
+  if (only && only[blockIdx.x] == 0) return;   // refactor only the boxes the tensor-core kernel marked
   using T = C<R>;
   constexpr bool SYM = LAY == LAY_SYM, TCL = LAY == LAY_TC;
   // S_{j+1} is kept in W2 when the stored copy is narrower than the arithmetic
@@ -428,30 +387,50 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
 }
 
 template <typename R, typename S, int LAY>
-static cudaError_t launch_factor_rs(hd_ctx *ctx, void *factor, void *work, cudaStream_t st) {
+static cudaError_t launch_factor_rs(hd_ctx *ctx, void *factor, void *work, const int32_t *only, cudaStream_t st) {
   const size_t smem = factor_smem_bytes(ctx->prec, ctx->max_m);
   cudaError_t e = cudaFuncSetAttribute(k_factor<R, S, LAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_factor<R, S, LAY><<<ctx->nsub, FT, smem, st>>>(ctx->d_subs, ctx->d_lpool, ctx->d_k2, ctx->NX, ctx->h * ctx->h,
                                              reinterpret_cast<S *>(factor), reinterpret_cast<C<R> *>(work),
-                                             ctx->d_status);
+                                             ctx->d_status, only);
   return cudaGetLastError();
 }
 
 template <typename R, typename S>
-static cudaError_t launch_factor_r(hd_ctx *ctx, void *factor, void *work, cudaStream_t st) {
-  if (ctx->sym) return launch_factor_rs<R, S, LAY_SYM>(ctx, factor, work, st);
-  return launch_factor_rs<R, S, LAY_FULL>(ctx, factor, work, st);
+static cudaError_t launch_factor_r(hd_ctx *ctx, void *factor, void *work, const int32_t *only, cudaStream_t st) {
+  if (ctx->sym) return launch_factor_rs<R, S, LAY_SYM>(ctx, factor, work, only, st);
+  return launch_factor_rs<R, S, LAY_FULL>(ctx, factor, work, only, st);
 }
 
+static cudaError_t launch_factor_simt(hd_ctx *ctx, void *factor, void *work, const int32_t *only, cudaStream_t st) {
+  return ctx->tc                  ? launch_factor_rs<float, float2, LAY_TC>(ctx, factor, work, only, st)
+         : ctx->prec == HD_C64   ? launch_factor_r<float, float2>(ctx, factor, work, only, st)
+         : ctx->prec == HD_C64_H ? launch_factor_r<float, __half2>(ctx, factor, work, only, st)
+                                 : launch_factor_r<double, double2>(ctx, factor, work, only, st);
+}
+
+// The tensor-core kernel where it applies (complex FP32 arithmetic, boxes up to 192
+// wide, unless the SIMT kernel was selected), followed by the pivoted SIMT kernel on
+// the boxes it marked (a launch whose other CTAs return at once); otherwise the SIMT
+// kernel on every box.
 int run_factor(hd_ctx *ctx, void *factor, void *work, cudaStream_t st) {
+  const bool tcore = ctx->fpath != HD_FACTOR_SIMT && factor_tc_supported(ctx);
+  if (ctx->fpath == HD_FACTOR_TCORE && !tcore) {
+    set_error("hd_factor_subdomains: the tensor-core factorisation needs complex FP32 factors and boxes at most 192 wide");
+    return HD_ERR_INVALID;
+  }
   tic(ctx, T_FACTOR, st);
-  cudaError_t e = ctx->tc                ? launch_factor_rs<float, float2, LAY_TC>(ctx, factor, work, st)
-                  : ctx->prec == HD_C64  ? launch_factor_r<float, float2>(ctx, factor, work, st)
-                  : ctx->prec == HD_C64_H ? launch_factor_r<float, __half2>(ctx, factor, work, st)
-                                          : launch_factor_r<double, double2>(ctx, factor, work, st);
-  toc(ctx, T_FACTOR, st, 1);
-  if (e != cudaSuccess) return cuda_fail(e, "k_factor launch");
+  cudaError_t e = cudaSuccess;
+  if (tcore) {
+    e = launch_factor_tc(ctx, factor, st);
+    if (e == cudaSuccess) e = launch_factor_simt(ctx, factor, work, ctx->d_fflag, st);
+  } else {
+    e = launch_factor_simt(ctx, factor, work, nullptr, st);
+  }
+  toc(ctx, T_FACTOR, st, tcore ? 2 : 1);
+  if (e != cudaSuccess) return cuda_fail(e, "factorisation launch");
+  ctx->last_fpath = tcore ? HD_FACTOR_TCORE : HD_FACTOR_SIMT;
   return HD_OK;
 }
 

@@ -136,6 +136,48 @@ template <> __device__ __forceinline__ float2 load_c<float2, __half2>(__half2 v)
 inline size_t store_bytes(int prec) { return prec == HD_C128 ? 16 : (prec == HD_C64 ? 8 : 4); }
 inline size_t compute_bytes(int prec) { return prec == HD_C128 ? 16 : 8; }
 
+// Entries of D_j (tridiagonal) and the coupling L_j of grid row j, Eq. (pml)
+// discretised with the box's own PML tables.
+template <typename T, typename R>
+__device__ __forceinline__ T d_entry(int r, int c, int j, const double2 *a1c, const double2 *ia1f, const double2 *a2c,
+                                     const double2 *ia2f, const double *k2row, double h2) {
+  const double2 a2 = a2c[j];
+  if (r == c) {
+    const double2 a1 = a1c[r];
+    const double2 cw = cmul(a2, ia1f[r]), ce = cmul(a2, ia1f[r + 1]);
+    const double2 cs = cmul(a1, ia2f[j]), cn = cmul(a1, ia2f[j + 1]);
+    const double2 j12 = cmul(a1, a2);
+    const double hk = mul_rn(h2, k2row[r]);
+    return mk<T>((R)(-(cw.x + ce.x + cs.x + cn.x) + hk * j12.x), (R)(-(cw.y + ce.y + cs.y + cn.y) + hk * j12.y));
+  }
+  if (r == c + 1) {
+    const double2 cw = cmul(a2, ia1f[r]);      // row r couples to column r-1 (west)
+    return mk<T>((R)cw.x, (R)cw.y);
+  }
+  if (r + 1 == c) {
+    const double2 ce = cmul(a2, ia1f[r + 1]);  // row r couples to column r+1 (east)
+    return mk<T>((R)ce.x, (R)ce.y);
+  }
+  return mk<T>(0, 0);
+}
+
+// d_entry restricted to its tridiagonal band (zero elsewhere without touching the tables)
+template <typename T, typename R>
+__device__ __forceinline__ T d_band(int r, int c, int j, const double2 *a1c, const double2 *ia1f, const double2 *a2c,
+                                    const double2 *ia2f, const double *k2row, double h2) {
+  return (r - c <= 1 && c - r <= 1) ? d_entry<T, R>(r, c, j, a1c, ia1f, a2c, ia2f, k2row, h2) : mk<T>(0, 0);
+}
+
+// Storage layouts of the S_j^{-1}: full column-major blocks, upper 16 x 16 tiles,
+// or TF32 real/imaginary planes in the tensor-core operand layout (HD_TCORE).
+enum { LAY_FULL = 0, LAY_SYM = 1, LAY_TC = 2 };
+
+__device__ __forceinline__ float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 // ---------------------------------------------------------------- tables
 // One overlapping box Omega_ij (global cell indices) and its owned box.
 struct SubDev {
@@ -203,6 +245,10 @@ struct hd_ctx {
   hd::AxisDev *d_axx = nullptr, *d_axy = nullptr;
   int32_t *d_nearx = nullptr, *d_neary = nullptr;  // per global index: box column/row nearest
   int32_t *d_status = nullptr;                    // device status word
+  int32_t *d_fflag = nullptr;                     // per box: 1 if the tensor-core factorisation marked it
+  int fpath = 0;                                  // hd_factor_path of hd_set_factor_path
+  double fpivot = 0.5;                            // pivot ratio of the tensor-core factorisation's check
+  int last_fpath = -1;                            // kernel of the last factorisation (1 SIMT, 2 tensor cores)
   cudaStream_t stream = nullptr;                  // set-up stream: the context's tables are freed on it
   std::vector<double> host_stat = std::vector<double>(8);   // host mirror of small device results
   std::vector<unsigned char> host_buf;            // per-solve host mirror (grows on demand)
@@ -265,4 +311,8 @@ int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cud
 int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const hd_gmres_opts *o, void *kws,
                     void *scratch, hd_gmres_stats *stats, cudaStream_t st);
 size_t factor_smem_bytes(int prec, int max_m);
+// Tensor-core factorisation (hd_factor_tc.cu): complex FP32 arithmetic, boxes up to 192 wide.
+bool factor_tc_supported(const hd_ctx *ctx);
+cudaError_t launch_factor_tc(hd_ctx *ctx, void *factor, cudaStream_t st);
+size_t factor_tc_smem_bytes();
 }  // namespace hd

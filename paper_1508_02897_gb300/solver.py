@@ -38,7 +38,8 @@ class HelmholtzDDM:
                  precision: str = "c64", cut_x: Optional[Sequence[int]] = None, cut_y: Optional[Sequence[int]] = None,
                  own_global_pml: bool = True, sigma0_over_omega: float = 20.0, pml_power: int = 2,
                  device: str = "cuda", stream: Optional[torch.cuda.Stream] = None, factor: bool = True,
-                 symmetric: bool = True, tcore: bool = False, smoothing: bool = False):
+                 symmetric: bool = True, tcore: bool = False, smoothing: bool = False,
+                 factor_path: str = "auto", pivot_ratio: float = 0.5):
         if not torch.cuda.is_available():
             raise RuntimeError("HelmholtzDDM needs a CUDA device: there is no CPU path")
         self.N, self.npml, self.n = N, npml, N + 2 * npml
@@ -61,6 +62,8 @@ class HelmholtzDDM:
             self.scratch = torch.empty(max(sb, 16), dtype=torch.uint8, device=self.device)
         self._krylov = {}
         self.factored = False
+        B.hd_set_factor_path(self.ctx, {"auto": B.HD_FACTOR_AUTO, "simt": B.HD_FACTOR_SIMT,
+                                        "tcore": B.HD_FACTOR_TCORE}[factor_path], pivot_ratio)
         if factor:
             self.factor()
 
@@ -71,6 +74,10 @@ class HelmholtzDDM:
         B.hd_factor_subdomains(self.ctx, self.factor_buf.data_ptr(), self.factor_bytes, self.scratch.data_ptr(),
                                self.scratch_bytes, self._st())
         self.factored = True
+
+    def factor_report(self):
+        """(boxes kept from the tensor-core factorisation, boxes factorised with partial pivoting)."""
+        return B.hd_factor_report(self.ctx, self._st())
 
     def autotune(self):
         """Picks the substitution launch shape by timing (cached per shape for the process)."""

@@ -11,6 +11,9 @@ CASES = {
     "ragged": dict(N=100, npml=8, nb=3, overlap=5, medium="random", cuts=[8, 8 + 29, 8 + 71, 108], seed=5),
     # 4x4 boxes over three layers
     "layers4": dict(N=128, npml=16, nb=4, overlap=8, medium="three_layer", cuts=None, seed=1),
+    # boxes wider than 128 (160, 178, 150): the factorisation's bottom-right block and
+    # ragged last panels; 178 is the widest box that needs a 178 x 178 Schur block
+    "wide": dict(N=360, npml=16, nb=3, overlap=8, medium="random", cuts=[16, 136, 266, 376], seed=9),
 }
 
 
