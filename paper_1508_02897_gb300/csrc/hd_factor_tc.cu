@@ -75,42 +75,49 @@ constexpr size_t kOffL = kOffG + sizeof(float2) * 2 * FX_KP * FX_KP;
 constexpr size_t kOffM = kOffL + sizeof(float2) * FX_ROWS;
 constexpr size_t kSmem = kOffM + 32;
 
-// x = h + m + l with BF16 pieces rounded to nearest (each remainder is exact in FP32).
-__device__ __forceinline__ void split3(float x, uint16_t &h, uint16_t &m, uint16_t &l) {
-  const __nv_bfloat16 bh = __float2bfloat16_rn(x);
-  const float r1 = __fsub_rn(x, __bfloat162float(bh));
-  const __nv_bfloat16 bm = __float2bfloat16_rn(r1);
-  const float r2 = __fsub_rn(r1, __bfloat162float(bm));
-  const __nv_bfloat16 bl = __float2bfloat16_rn(r2);
-  h = __bfloat16_as_ushort(bh);
-  m = __bfloat16_as_ushort(bm);
-  l = __bfloat16_as_ushort(bl);
+// (x0, x1) = h + m + l piecewise, BF16 pieces rounded to nearest (each remainder is
+// exact in FP32), two values per conversion instruction; the pieces come packed as
+// BF16 pairs (x0 in the low half).
+__device__ __forceinline__ void split3x2(float x0, float x1, uint32_t &h, uint32_t &m, uint32_t &l) {
+  const __nv_bfloat162 bh = __floats2bfloat162_rn(x0, x1);
+  const float2 fh = __bfloat1622float2(bh);
+  const float r0 = __fsub_rn(x0, fh.x), r1 = __fsub_rn(x1, fh.y);
+  const __nv_bfloat162 bm = __floats2bfloat162_rn(r0, r1);
+  const float2 fm = __bfloat1622float2(bm);
+  const __nv_bfloat162 bl = __floats2bfloat162_rn(__fsub_rn(r0, fm.x), __fsub_rn(r1, fm.y));
+  h = *reinterpret_cast<const uint32_t *>(&bh);
+  m = *reinterpret_cast<const uint32_t *>(&bm);
+  l = *reinterpret_cast<const uint32_t *>(&bl);
 }
 
-// Row r of an operand tile (16 BF16 values) in the no-swizzle K-major layout: 8-row
-// groups 256 bytes apart (SBO), the two 8-column core matrices 128 bytes apart (LBO).
-__device__ __forceinline__ void put_row(unsigned char *tile, int r, const uint16_t *v) {
+// Row r of an operand tile (16 BF16 values as 8 pairs) in the no-swizzle K-major layout:
+// 8-row groups 256 bytes apart (SBO), the two 8-column core matrices 128 bytes apart (LBO).
+__device__ __forceinline__ void put_row(unsigned char *tile, int r, const uint32_t *v) {
   unsigned char *p = tile + (r >> 3) * 256 + (r & 7) * 16;
-  uint4 a, b;
-  a.x = v[0] | ((uint32_t)v[1] << 16); a.y = v[2] | ((uint32_t)v[3] << 16);
-  a.z = v[4] | ((uint32_t)v[5] << 16); a.w = v[6] | ((uint32_t)v[7] << 16);
-  b.x = v[8] | ((uint32_t)v[9] << 16); b.y = v[10] | ((uint32_t)v[11] << 16);
-  b.z = v[12] | ((uint32_t)v[13] << 16); b.w = v[14] | ((uint32_t)v[15] << 16);
-  *reinterpret_cast<uint4 *>(p) = a;
-  *reinterpret_cast<uint4 *>(p + 128) = b;
+  *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+  *reinterpret_cast<uint4 *>(p + 128) = make_uint4(v[4], v[5], v[6], v[7]);
 }
 
 // Splits 16 values and writes the three pieces as row r of tiles t, t+1, t+2.
 __device__ __forceinline__ void put_split(unsigned char *tiles, uint32_t tile_bytes, int t, int r, const float *v) {
-  uint16_t h[16], m[16], l[16];
+  uint32_t h[8], m[8], l[8];
 #pragma unroll
-  for (int i = 0; i < 16; ++i) split3(v[i], h[i], m[i], l[i]);
+  for (int i = 0; i < 8; ++i) split3x2(v[2 * i], v[2 * i + 1], h[i], m[i], l[i]);
   put_row(tiles + (size_t)t * tile_bytes, r, h);
   put_row(tiles + (size_t)(t + 1) * tile_bytes, r, m);
   put_row(tiles + (size_t)(t + 2) * tile_bytes, r, l);
 }
 
 __device__ __forceinline__ float cabs2f(float2 a) { return a.x * a.x + a.y * a.y; }
+
+// 1 / x for the pivots: the hardware approximation refined by one Newton step
+// (r (2 - x r)), within about one ulp for normal x; a zero or non-finite x is caught by
+// the pivot check before the result matters.
+__device__ __forceinline__ float recip(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r * fmaf(-x, r, 2.f);
+}
 
 // Stored entry (r, c) of S_j^{-1} in the full or tensor-core layouts (zero outside m x m).
 template <typename S, int LAY>
@@ -190,42 +197,34 @@ k_factor_tc(const SubDev *__restrict__ subs, int nsub, const double2 *__restrict
       reinterpret_cast<uint4 *>(smem_raw)[i] = make_uint4(0u, 0u, 0u, 0u);
     if (tid == 0) *sflag = 0;
 
-    // ---- S_0 = D_0 into tensor memory
-    {
+    // ---- S_0 = D_0 into tensor memory (the three band entries of a row computed once)
+    if (warp < 4 || (warp < 6 && mb > 0)) {
       const double *k2row = k2 + (int64_t)s.ey0 * NX + s.ex0;
-      if (warp < 4) {
-        const int r = tid;
-        for (int cc = 0; cc < NP; cc += 16) {
-          float re[16], im[16];
+      const bool top = warp < 4;
+      const int r = tid;   // top: rows 0..127; warps 4, 5: rows 128 + (tid - 128)
+      const int ncol = top ? NP : NB, cbase = top ? 0 : 128;
+      const uint32_t tre = top ? tq : tq + 2 * NP, tim = top ? tq + NP : tq + 2 * NP + NB;
+      float2 dband[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+      if (r < m)
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int c = cc + i;
-            const float2 v = (r < m && c < m) ? d_band<float2, float>(r, c, 0, a1c, ia1f, a2c, ia2f, k2row, h2)
-                                              : make_float2(0.f, 0.f);
-            re[i] = v.x;
-            im[i] = v.y;
-          }
-          tc::tmem_st16(tq + cc, re);
-          tc::tmem_st16(tq + NP + cc, im);
+        for (int t = 0; t < 3; ++t) {
+          const int c = r - 1 + t;
+          if (c >= 0 && c < m) dband[t] = d_entry<float2, float>(r, c, 0, a1c, ia1f, a2c, ia2f, k2row, h2);
         }
-      } else if (warp < 6 && mb > 0) {
-        const int r = 128 + tid - 128;   // bottom rows: lane tid - 128 of quarters 0 and 1
-        for (int cc = 0; cc < NB; cc += 16) {
-          float re[16], im[16];
+      for (int cc = 0; cc < ncol; cc += 16) {
+        float re[16], im[16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int c = 128 + cc + i;
-            const float2 v = (r < m && c < m) ? d_band<float2, float>(r, c, 0, a1c, ia1f, a2c, ia2f, k2row, h2)
-                                              : make_float2(0.f, 0.f);
-            re[i] = v.x;
-            im[i] = v.y;
-          }
-          tc::tmem_st16(tq + 2 * NP + cc, re);
-          tc::tmem_st16(tq + 2 * NP + NB + cc, im);
+        for (int i = 0; i < 16; ++i) {
+          const int t = cbase + cc + i - r + 1;   // band position 0, 1, 2, or outside
+          const float2 v = t == 0 ? dband[0] : (t == 1 ? dband[1] : (t == 2 ? dband[2] : make_float2(0.f, 0.f)));
+          re[i] = v.x;
+          im[i] = v.y;
         }
+        tc::tmem_st16(tre + cc, re);
+        tc::tmem_st16(tim + cc, im);
       }
-      tc::tmem_wait_st();
     }
+    tc::tmem_wait_st();
 
     for (int j = 0; j < rows && alive; ++j) {
       const bool more = j + 1 < rows;
@@ -284,80 +283,114 @@ k_factor_tc(const SubDev *__restrict__ subs, int nsub, const double2 *__restrict
         }
         __syncthreads();
 
-        // ---- B. P = C_K^{-1} (w x w) by Gauss-Jordan without pivoting, with the pivot check
+        // ---- B. the A operand, which needs C only: A = -X, X = C outside rows K and zero on
+        //         rows K (their new values are stored directly), one row per thread; and the
+        //         first pivot of the panel against every unprocessed row below the panel
+        {
+          const int r = tid, kr = r - k0;
+          if (r < FX_ROWS && r < m) {
+            const bool inK = kr >= 0 && kr < w;
+            float vr[16], vi[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float2 c = Cs[r * CLD + i];
+              vr[i] = inK ? 0.f : -c.x;
+              vi[i] = inK ? 0.f : -c.y;
+            }
+            put_split(At, FX_ATILE, 0, r, vr);
+            put_split(At, FX_ATILE, 3, r, vi);
+            if (r >= k0 + w && !(cabs2f(Cs[k0 * CLD]) >= tau2 * cabs2f(Cs[r * CLD]))) *sflag = 1;
+          }
+        }
+        // ---- P = C_K^{-1} (w x w) by Gauss-Jordan without pivoting, one entry per thread
+        //      (i, jj) = (tid / 16, tid % 16), two alternating shared copies.  Two elimination
+        //      steps k, k+1 per barrier: every thread loads the nine entries it needs and
+        //      applies both in-place steps to its own entry (the same arithmetic as two
+        //      separate steps).  Each pivot is checked by the threads of the unprocessed
+        //      entries below it.
         {
           const int i = tid >> 4, jj = tid & 15;
-          G[tid] = (i < w && jj < w) ? Cs[(k0 + i) * CLD + jj] : make_float2(i == jj ? 1.f : 0.f, 0.f);
-          if (warp == 7) {
-            // first pivot against every unprocessed row below the panel
-            float mx = 0.f;
-            for (int r = k0 + w + lane; r < m; r += 32) mx = fmaxf(mx, cabs2f(Cs[r * CLD]));
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-            const float p2 = cabs2f(Cs[k0 * CLD]);
-            if (lane == 0 && !(p2 >= tau2 * mx)) *sflag = 1;
-          }
+          float2 *B0 = G, *B1 = G + 256;
+          B0[tid] = (i < w && jj < w) ? Cs[(k0 + i) * CLD + jj] : make_float2(i == jj ? 1.f : 0.f, 0.f);
           __syncthreads();
-          for (int k = 0; k < w; ++k) {
-            const float2 *src = G + (k & 1) * 256;
-            float2 *dst = G + ((k + 1) & 1) * 256;
-            const float2 piv = src[k * 16 + k];
-            const float2 ip = cinv(piv);
-            if (tid == 0) {
-              float mx = 0.f;
-              for (int q = k + 1; q < w; ++q) mx = fmaxf(mx, cabs2f(src[q * 16 + k]));
-              const float p2 = cabs2f(piv);
-              if (!(p2 >= tau2 * mx) || !(p2 > 0.f) || !isfinite(p2)) *sflag = 1;
+          // in-place Gauss-Jordan value of entry (x, y) after the step with pivot index k and
+          // inverse pivot ip: a_xy the entry, a_xk its pivot-column entry, a_ky its pivot-row entry
+          auto gj = [](int x, int y, int k, float2 a_xy, float2 a_xk, float2 a_ky, float2 ip) -> float2 {
+            if (x == k) return y == k ? ip : cmul(a_ky, ip);
+            if (y == k) {
+              const float2 v = cmul(a_xk, ip);
+              return make_float2(-v.x, -v.y);
             }
-            const float2 aik = src[i * 16 + k], akj = src[k * 16 + jj], aij = src[tid];
-            float2 v;
-            if (i == k) v = jj == k ? ip : cmul(akj, ip);
-            else if (jj == k) { v = cmul(aik, ip); v.x = -v.x; v.y = -v.y; }
-            else v = cfms(aik, cmul(akj, ip), aij);
+            return cfms(a_xk, cmul(a_ky, ip), a_xy);
+          };
+          int par = 0;
+#pragma unroll 1
+          for (int k = 0; k < w; k += 2, par ^= 1) {
+            const float2 *src = par ? B1 : B0;
+            float2 *dst = par ? B0 : B1;
+            const float2 piv = src[k * 16 + k], aik = src[i * 16 + k], akj = src[k * 16 + jj], aij = src[tid];
+            const float p2 = cabs2f(piv);
+            if (jj == k && i > k && i < w && !(p2 >= tau2 * cabs2f(aik))) *sflag = 1;
+            if (tid == 0 && (!(p2 > 0.f) || !isfinite(p2))) *sflag = 1;
+            const float rd = recip(p2);   // 1 / pivot = conj(pivot) / |pivot|^2
+            const float2 ip = make_float2(piv.x * rd, -piv.y * rd);
+            float2 v = gj(i, jj, k, aij, aik, akj, ip);
+            const int k1 = k + 1;
+            if (k1 < w) {
+              // the second step on the values after the first
+              const float2 a_i1 = src[i * 16 + k1], a_k1 = src[k * 16 + k1];
+              const float2 a_1j = src[k1 * 16 + jj], a_1k = src[k1 * 16 + k], a_11 = src[k1 * 16 + k1];
+              const float2 vi1 = gj(i, k1, k, a_i1, aik, a_k1, ip);     // entry (i, k+1)
+              const float2 v1j = gj(k1, jj, k, a_1j, a_1k, akj, ip);    // entry (k+1, jj)
+              const float2 piv1 = gj(k1, k1, k, a_11, a_1k, a_k1, ip);  // next pivot
+              const float q2 = cabs2f(piv1);
+              if (jj == k1 && i > k1 && i < w && !(q2 >= tau2 * cabs2f(vi1))) *sflag = 1;
+              if (tid == 0 && (!(q2 > 0.f) || !isfinite(q2))) *sflag = 1;
+              const float rd1 = recip(q2);
+              const float2 ip1 = make_float2(piv1.x * rd1, -piv1.y * rd1);
+              v = gj(i, jj, k1, v, vi1, v1j, ip1);
+            }
             dst[tid] = v;
             __syncthreads();
           }
+          // P into the first copy, zero outside w x w
+          const float2 *res = par ? B1 : B0;
+          const float2 pv = (i < w && jj < w) ? res[tid] : make_float2(0.f, 0.f);
+          __syncthreads();
+          B0[tid] = pv;
+          __syncthreads();
         }
-        const float2 *Pm = G + (w & 1) * 256;   // P[i][kk] at Pm[i * 16 + kk]
+        const float2 *Pm = G;   // P[i][kk] at Pm[i * 16 + kk], zero outside w x w
 
-        // ---- C. operands: A = -X (X = C outside rows K, zero on rows K) and B = Y^T = Z P,
-        //         three BF16 pieces each; Y^T also replaces C in the panel copy
+        // ---- C. the B operand Y^T = Z P (three BF16 pieces); Y^T also replaces C in the panel copy
         if (tid < FX_ROWS && tid < m) {
           const int r = tid, kr = r - k0;
           const bool inK = kr >= 0 && kr < w;
-          float2 c[16];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) c[i] = Cs[r * CLD + i];
           float vr[16], vi[16];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            vr[i] = inK ? 0.f : -c[i].x;
-            vi[i] = inK ? 0.f : -c[i].y;
-          }
-          put_split(At, FX_ATILE, 0, r, vr);
-          put_split(At, FX_ATILE, 3, r, vi);
           float2 y[16];
           if (inK) {
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-              float2 p = make_float2(0.f, 0.f);
-#pragma unroll
-              for (int q = 0; q < 16; ++q)
-                if (q == kr) p = Pm[q * 16 + kk];
-              y[kk] = (kk < w) ? p : make_float2(0.f, 0.f);
-            }
+            for (int kk = 0; kk < 16; ++kk) y[kk] = Pm[kr * 16 + kk];
           } else {
-            const float zs = r < k0 ? -1.f : 1.f;
+            // y = zs C[r] P: q outer, 16 independent accumulator chains
 #pragma unroll
-            for (int kk = 0; kk < 16; ++kk) {
-              float2 acc = make_float2(0.f, 0.f);
-              if (kk < w) {
+            for (int kk = 0; kk < 16; ++kk) y[kk] = make_float2(0.f, 0.f);
+            // kept as a loop over q (16 independent accumulators per step): a fully
+            // unrolled copy is 1024 FMAs of straight-line code in an already large kernel
+#pragma unroll 1
+            for (int q = 0; q < 16; ++q) {
+              const float4 *prow = reinterpret_cast<const float4 *>(Pm + q * 16);
+              const float2 cq = Cs[r * CLD + q];
 #pragma unroll
-                for (int q = 0; q < 16; ++q)
-                  if (q < w) acc = cfma(c[q], Pm[q * 16 + kk], acc);
+              for (int k2 = 0; k2 < 8; ++k2) {
+                const float4 pp = prow[k2];
+                y[2 * k2] = cfma(cq, make_float2(pp.x, pp.y), y[2 * k2]);
+                y[2 * k2 + 1] = cfma(cq, make_float2(pp.z, pp.w), y[2 * k2 + 1]);
               }
-              y[kk] = make_float2(zs * acc.x, zs * acc.y);
             }
+            if (r < k0)
+#pragma unroll
+              for (int kk = 0; kk < 16; ++kk) y[kk] = make_float2(-y[kk].x, -y[kk].y);
           }
 #pragma unroll
           for (int kk = 0; kk < 16; ++kk) {
@@ -378,38 +411,53 @@ k_factor_tc(const SubDev *__restrict__ subs, int nsub, const double2 *__restrict
         // warp-collective, so the warp holding rows K rewrites whole rows: its other lanes
         // store back what they hold (zero in the columns K).
         {
-          const bool kwarp_top = warp < 4 && (k0 >> 5) == warp && k0 < 128;
-          const bool kwarp_bot = warp >= 4 && warp < 6 && k0 >= 128 && ((k0 - 128) >> 5) == warp - 4;
-          const bool zwarp = (warp < 4) || (warp < 6 && k0 >= 128);
-          if (kwarp_top || kwarp_bot) {
-            const int kr = tid - k0;   // top: row tid; bottom: row 128 + (tid - 128) = tid
-            const bool inK = kr >= 0 && kr < w;
-            const int ncol = kwarp_top ? NP : NB, cb = kwarp_top ? 0 : 128, kc = k0 - cb;
-            const uint32_t tre = kwarp_top ? tq : tq + 2 * NP, tim = kwarp_top ? tq + NP : tq + 2 * NP + NB;
-            for (int cc = 0; cc < ncol; cc += 16) {
-              float re[16], im[16];
-              tc::tmem_ld16(tre + cc, re);
-              tc::tmem_ld16(tim + cc, im);
-#pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                if (inK) {
-                  const float2 v = Cs[(cb + cc + i) * CLD + kr];
-                  re[i] = v.x;
-                  im[i] = v.y;
-                } else if (cc == kc) {
-                  re[i] = 0.f;
-                  im[i] = 0.f;
-                }
-              }
-              tc::tmem_st16(tre + cc, re);
-              tc::tmem_st16(tim + cc, im);
-            }
-          } else if (zwarp) {
+          const int q = warp & 3;
+          const bool top_rmw = k0 < 128 && q == (k0 >> 5);
+          const bool bot_rmw = k0 >= 128 && q == ((k0 - 128) >> 5);
+          // columns K of rows outside K: zero (top rows: warps 0-3; bottom rows: warps 4, 5)
+          if (warp < 4 && !top_rmw) {
             const float z[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            const uint32_t base = warp < 4 ? tq + k0 : tq + 2 * NP + (k0 - 128);
-            const uint32_t off = warp < 4 ? NP : NB;
-            tc::tmem_st16(base, z);
-            tc::tmem_st16(base + off, z);
+            tc::tmem_st16(tq + k0, z);
+            tc::tmem_st16(tq + NP + k0, z);
+          } else if ((warp == 4 || warp == 5) && k0 >= 128 && !bot_rmw) {
+            const float z[16] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            tc::tmem_st16(tq + 2 * NP + (k0 - 128), z);
+            tc::tmem_st16(tq + 2 * NP + NB + (k0 - 128), z);
+          }
+          if (top_rmw || bot_rmw) {
+            // the two warps of this lane quarter rewrite the rows of K, half the columns each
+            const int rrow = top_rmw ? 32 * q + lane : 128 + 32 * q + lane;
+            const int kr = rrow - k0;
+            const bool inK = kr >= 0 && kr < w;
+            const int ncol = top_rmw ? NP : NB, cb = top_rmw ? 0 : 128, kc = k0 - cb;
+            const int nch = ncol / 16, half = (nch + 1) / 2;
+            const int ch0 = warp < 4 ? 0 : half, ch1 = warp < 4 ? half : nch;
+            const uint32_t tre = top_rmw ? tq : tq + 2 * NP, tim = top_rmw ? tq + NP : tq + 2 * NP + NB;
+            for (int c2 = ch0; c2 < ch1; c2 += 2) {
+              float re[2][16], im[2][16];
+              const int nh = c2 + 1 < ch1 ? 2 : 1;   // chunks of 16 columns in this pass, one wait
+              for (int hh = 0; hh < nh; ++hh) {
+                tc::tmem_ld16_nw(tre + 16 * (c2 + hh), re[hh]);
+                tc::tmem_ld16_nw(tim + 16 * (c2 + hh), im[hh]);
+              }
+              tc::tmem_wait_ld();
+              for (int hh = 0; hh < nh; ++hh) {
+                const int cc = 16 * (c2 + hh);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  if (inK) {
+                    const float2 v = Cs[(cb + cc + i) * CLD + kr];
+                    re[hh][i] = v.x;
+                    im[hh][i] = v.y;
+                  } else if (cc == kc) {
+                    re[hh][i] = 0.f;
+                    im[hh][i] = 0.f;
+                  }
+                }
+                tc::tmem_st16(tre + cc, re[hh]);
+                tc::tmem_st16(tim + cc, im[hh]);
+              }
+            }
           }
         }
         tc::tmem_wait_st();
@@ -441,7 +489,7 @@ k_factor_tc(const SubDev *__restrict__ subs, int nsub, const double2 *__restrict
           }
           tc::mma_commit(mbar);
         }
-        const bool ok = tc::bar_wait(mbar, nphase & 1u, abort_flag);
+        const bool ok = tc::bar_spin(mbar, nphase & 1u, abort_flag);
         ++nphase;
         tc::fence_after();
         if (__syncthreads_or(!ok)) {
@@ -459,52 +507,87 @@ k_factor_tc(const SubDev *__restrict__ subs, int nsub, const double2 *__restrict
       S *slot = Fs + (int64_t)j * slot_elems;
       const double *k2row = k2 + (int64_t)(s.ey0 + j + 1) * NX + s.ex0;
       const int ldm = s.ldm;
-      if (warp < 4 || (warp < 6 && mb > 0)) {
-        const bool top = warp < 4;
-        const int r = top ? tid : tid;   // bottom rows: 128 + (tid - 128)
-        const int ncol = top ? NP : NB;
-        const int cbase = top ? 0 : 128;
-        const uint32_t tre = top ? tq : tq + 2 * NP, tim = top ? tq + NP : tq + 2 * NP + NB;
-        const int I = r >> 4, rr = r & 15;
-        for (int cc = 0; cc < ncol; cc += 16) {
-          float re[16], im[16];
-          tc::tmem_ld16(tre + cc, re);
-          tc::tmem_ld16(tim + cc, im);
-          const int c0 = cbase + cc;
-          if (LAY == LAY_SYM) {
-            const int J = c0 >> 4;
-            if (J >= I && r < 16 * mt) {
-              S *tile = slot + (int64_t)(J * (J + 1) / 2 + I) * 256;
+      // every warp takes part: warps 0-3 the left columns of their rows 0..127, warps 4-7 the
+      // right columns of the same rows, warps 4 and 5 also the bottom-right block (rows
+      // 128..m-1), the column split balancing the 16-column chunks
+      {
+        const int q = warp & 3;
+        const int nchT = NP / 16, nchB = NB / 16, sT = (nchT + nchB + 1) / 2;
+        for (int reg = 0; reg < 2; ++reg) {
+          const bool top = reg == 0;
+          int ch0, ch1;
+          if (top) {
+            ch0 = warp < 4 ? 0 : min(sT, nchT);
+            ch1 = warp < 4 ? min(sT, nchT) : nchT;
+          } else {
+            ch0 = 0;
+            ch1 = (warp == 4 || warp == 5) ? nchB : 0;
+          }
+          if (ch0 >= ch1) continue;
+          const int r = top ? 32 * q + lane : 128 + 32 * q + lane;
+          const int cbase = top ? 0 : 128;
+          const uint32_t tre = top ? tq : tq + 2 * NP, tim = top ? tq + NP : tq + 2 * NP + NB;
+          const int I = r >> 4, rr = r & 15;
+          // the three entries of D_{j+1} in row r (west, centre, east), once per row
+          float2 dband[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          const float2 lr = lS[r];
+          if (more && r < m)
 #pragma unroll
-              for (int i = 0; i < 16; ++i) {
-                const int c = c0 + i;
-                const float2 v = (r < m && c < m) ? make_float2(re[i], im[i]) : make_float2(0.f, 0.f);
-                if (J > I || i >= rr) tile[i * 16 + ((rr + i) & 15)] = store_c<S>(v);
-                if (J == I && i > rr) tile[rr * 16 + ((i + rr) & 15)] = store_c<S>(v);
+            for (int t = 0; t < 3; ++t) {
+              const int c = r - 1 + t;
+              if (c >= cbase + 16 * ch0 - 1 && c <= cbase + 16 * ch1 && c >= 0 && c < m)
+                dband[t] = d_entry<float2, float>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2);
+            }
+          for (int c2 = ch0; c2 < ch1; c2 += 2) {
+            float rb[2][16], ib[2][16];
+            const int nh = c2 + 1 < ch1 ? 2 : 1;   // chunks of 16 columns in this pass, one wait
+            for (int hh = 0; hh < nh; ++hh) {
+              tc::tmem_ld16_nw(tre + 16 * (c2 + hh), rb[hh]);
+              tc::tmem_ld16_nw(tim + 16 * (c2 + hh), ib[hh]);
+            }
+            tc::tmem_wait_ld();
+            for (int hh = 0; hh < nh; ++hh) {
+              const int cc = 16 * (c2 + hh);
+              float *re = rb[hh], *im = ib[hh];
+              const int c0 = cbase + cc;
+              if (LAY == LAY_SYM) {
+                const int J = c0 >> 4;
+                if (J >= I && r < 16 * mt) {
+                  S *tile = slot + (int64_t)(J * (J + 1) / 2 + I) * 256;
+#pragma unroll
+                  for (int i = 0; i < 16; ++i) {
+                    const int c = c0 + i;
+                    const float2 v = (r < m && c < m) ? make_float2(re[i], im[i]) : make_float2(0.f, 0.f);
+                    if (J > I || i >= rr) tile[i * 16 + ((rr + i) & 15)] = store_c<S>(v);
+                    if (J == I && i > rr) tile[rr * 16 + ((i + rr) & 15)] = store_c<S>(v);
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  const int c = c0 + i;
+                  const float2 v = make_float2(re[i], im[i]);
+                  emit<S, LAY>(slot, r, c, v, m, ldm, mp8);
+                  if (top && c >= 128) emit<S, LAY>(slot, c, r, v, m, ldm, mp8);   // bottom-left block
+                }
+              }
+              if (more) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                  const int c = c0 + i;
+                  float2 v = make_float2(0.f, 0.f);
+                  if (r < m && c < m) {
+                    const int t = c - r + 1;   // band position 0, 1, 2, or outside
+                    const float2 d = t == 0 ? dband[0] : (t == 1 ? dband[1] : (t == 2 ? dband[2] : make_float2(0.f, 0.f)));
+                    v = cfms(cmul(lr, make_float2(re[i], im[i])), lS[c], d);
+                  }
+                  re[i] = v.x;
+                  im[i] = v.y;
+                }
+                tc::tmem_st16(tre + cc, re);
+                tc::tmem_st16(tim + cc, im);
               }
             }
-          } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int c = c0 + i;
-              const float2 v = make_float2(re[i], im[i]);
-              emit<S, LAY>(slot, r, c, v, m, ldm, mp8);
-              if (top && c >= 128) emit<S, LAY>(slot, c, r, v, m, ldm, mp8);   // bottom-left block
-            }
-          }
-          if (more) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int c = c0 + i;
-              float2 v = make_float2(0.f, 0.f);
-              if (r < m && c < m)
-                v = cfms(cmul(lS[r], make_float2(re[i], im[i])), lS[c],
-                         d_band<float2, float>(r, c, j + 1, a1c, ia1f, a2c, ia2f, k2row, h2));
-              re[i] = v.x;
-              im[i] = v.y;
-            }
-            tc::tmem_st16(tre + cc, re);
-            tc::tmem_st16(tim + cc, im);
           }
         }
         tc::tmem_wait_st();
