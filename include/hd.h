@@ -227,9 +227,12 @@ typedef enum {
  * Same result as hd_apply_precond, but the staging vectors live in a fixed
  * 64 MiB device array inside the library instead of a caller workspace; every
  * GPU that loads the library holds that array until the process exits.  The
- * first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  A problem whose staging vectors need more than 64 MiB
+ * first call in a CUDA context (device and driver context, primary or made by
+ * the caller) looks up the array's device address there (cudaGetSymbolAddress)
+ * and remembers it for that context; make that first call before any stream
+ * capture.  A context destroyed by cudaDeviceReset whose replacement happens to
+ * get the same driver handle is not told apart, so after a reset make the next
+ * call through a fresh process or context.  A problem whose staging vectors need more than 64 MiB
  * (scratch_bytes of hd_query_workspace for the substitution) is refused with
  * HD_ERR_OOM.  Every call shares the one array and it keeps the last call's
  * contents (no entry is read before the same call writes it, so nothing needs
@@ -300,14 +303,6 @@ int hd_gmres_solve(hd_ctx *ctx, const void *b_dev, void *x_dev, int32_t nrhs, co
  * taken from the cache). */
 int hd_autotune(hd_ctx *ctx, const void *r_dev, void *z_dev, void *scratch_dev, size_t scratch_bytes,
                 int32_t *threads_out, int32_t *stages_out, float *ms_out, void *stream);
-
-/* Roofline denominators measured on the current device (no counterpart in the
- * paper): FP64 and FP32 FMA throughput (TFLOP/s, eight independent FMA chains
- * per thread) and a device-to-device copy through buf_dev (GB/s counting bytes
- * read plus written).  buf_dev: at least 64 MiB of scratch (1 GiB or more gives
- * a copy larger than L2).  Synchronises `stream`.  Outputs may be NULL. */
-int hd_probe_peaks(void *buf_dev, size_t buf_bytes, double *fp64_tflops, double *fp32_tflops, double *copy_gbs,
-                   void *stream);
 
 /* Per-kernel-class timing with CUDA events recorded on the launching stream
  * (events only while profiling is on; off by default).  Classes: 0

@@ -222,8 +222,18 @@ def factor_box(grid: Grid, k2: np.ndarray, s: Subdomain) -> BandLU:
 
 
 def oracle_threads() -> int:
-    """Threads that factorise boxes at once: HD_ORACLE_THREADS, else every host core."""
+    """Threads that factorise or solve boxes at once: HD_ORACLE_THREADS, else every host core."""
     return max(1, int(os.environ.get("HD_ORACLE_THREADS", "0")) or (os.cpu_count() or 1))
+
+
+_pools = {}
+
+
+def _pool(n: int) -> ThreadPoolExecutor:
+    """A process-wide thread pool of n workers (the banded solver releases the GIL)."""
+    if n not in _pools:
+        _pools[n] = ThreadPoolExecutor(max_workers=n)
+    return _pools[n]
 
 
 class DDMPreconditioner:
@@ -245,9 +255,8 @@ class DDMPreconditioner:
         self._A = None
         self.subs = decompose(grid, cut_x, cut_y, overlap, own_global_pml)
         self.active = list(range(len(self.subs))) if subdomains is None else list(subdomains)
-        nthr = min(threads or oracle_threads(), max(1, len(self.active)))
-        with ThreadPoolExecutor(max_workers=nthr) as ex:
-            lus = list(ex.map(lambda t: factor_box(grid, self.k2, self.subs[t]), self.active))
+        self.threads = min(threads or oracle_threads(), max(1, len(self.active)))
+        lus = list(_pool(self.threads).map(lambda t: factor_box(grid, self.k2, self.subs[t]), self.active))
         self.lu = dict(zip(self.active, lus))
 
     def local_solve(self, s_idx: int, r: np.ndarray) -> np.ndarray:
@@ -267,9 +276,10 @@ class DDMPreconditioner:
         sum_ij beta_ij u_ij^0 (the Remark after Eq. (pc))."""
         r = np.asarray(r, dtype=np.complex128).reshape(self.grid.n, self.grid.n)
         z = np.zeros_like(r)
-        for s_idx in self.active:
+        # the local solves are independent (threads); the sum runs in box order
+        sols = list(_pool(self.threads).map(lambda t: self.local_solve(t, r), self.active))
+        for s_idx, u in zip(self.active, sols):
             s = self.subs[s_idx]
-            u = self.local_solve(s_idx, r)
             z[s.ey0:s.ey1, s.ex0:s.ex1] += self.beta(s_idx) * u if self.smoothing else u
         return z
 
@@ -438,8 +448,9 @@ def block_fgmres(apply_A: Callable[[np.ndarray], np.ndarray], apply_M: Callable[
     Methods for Sparse Linear Systems*, 2nd ed., Sec. 6.12, made flexible as in Sec. 9.4).
 
     Per cycle: R = B - A X and R = V_0 S (thin QR, V_0 n x p); block Arnoldi step j:
-    Z_j = M V_j (M applied to every column), W = A Z_j, H_ij = V_i^H W and W -= V_i H_ij for
-    i <= j, applied twice (classical Gram-Schmidt), W = V_{j+1} H_{j+1,j} (thin QR); Y
+    Z_j = M V_j (M applied to every column), W = A Z_j, H_ij = V_i^H W for all i <= j from the
+    same W, then W -= sum_i V_i H_ij, the whole pass twice (block classical Gram-Schmidt, as
+    the point FGMRES), W = V_{j+1} H_{j+1,j} (thin QR); Y
     minimises || E_1 S - Hbar_j Y ||_F (least squares) and the column norms of that
     residual are the columns' residual estimates.  The cycle ends when every column's
     estimate is <= rtol ||b_c|| (or at the restart, or when a new block is rank
@@ -472,11 +483,11 @@ def block_fgmres(apply_A: Callable[[np.ndarray], np.ndarray], apply_M: Callable[
             Z.append(M_cols(V[j]))
             W = A_cols(Z[j])
             wnorm = np.linalg.norm(W)
-            for _ in range(2):
+            for _ in range(2):                               # classical: every H_ij from the same W
+                Hs = [V[i].conj().T @ W for i in range(j + 1)]
                 for i in range(j + 1):
-                    Hij = V[i].conj().T @ W
-                    W = W - V[i] @ Hij
-                    Hbar[i * p:(i + 1) * p, j * p:(j + 1) * p] += Hij
+                    W = W - V[i] @ Hs[i]
+                    Hbar[i * p:(i + 1) * p, j * p:(j + 1) * p] += Hs[i]
             Vn, Hn = np.linalg.qr(W)
             Hbar[(j + 1) * p:(j + 2) * p, j * p:(j + 1) * p] = Hn
             V.append(Vn)

@@ -94,7 +94,6 @@ _SIGS = {
     "hd_apply_precond_noalloc": [_P, _P, _P, ct.c_int32, _P],
     "hd_autotune": [_P, _P, _P, _P, ct.c_size_t, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
                     ct.POINTER(ct.c_float), _P],
-    "hd_probe_peaks": [_P, ct.c_size_t, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), _P],
     "hd_set_profiling": [_P, ct.c_int32],
     "hd_get_timers": [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32, ct.c_int32, _P],
     "hd_check_status": [_P, ct.c_int32, _P],
@@ -290,10 +289,3 @@ def hd_server_info(srv):
 
 def hd_server_destroy(srv):
     _check("hd_server_destroy", lib().hd_server_destroy(srv))
-
-
-def hd_probe_peaks(buf_ptr, buf_bytes, stream):
-    """(FP64 TFLOP/s, FP32 TFLOP/s, copy GB/s) measured on the current device."""
-    a, b, c = ct.c_double(), ct.c_double(), ct.c_double()
-    _check("hd_probe_peaks", lib().hd_probe_peaks(buf_ptr, buf_bytes, ct.byref(a), ct.byref(b), ct.byref(c), stream))
-    return a.value, b.value, c.value

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "hd_internal.cuh"
 
@@ -15,9 +16,11 @@
 // long-running services that must keep a fixed device footprint after
 // start-up.  For them the staging vectors live in one fixed device array
 // inside this library.  In host code the array's name is only a host-side
-// stand-in, so its device address is looked up once per device
-// (cudaGetSymbolAddress, with that device current, on the first call made on
-// that device) and passed to the kernels.  Every GPU that loads the library
+// stand-in, so its device address is looked up (cudaGetSymbolAddress, with the
+// device current) the first time a call runs in a given CUDA context, and
+// passed to the kernels.  The lookup is remembered per context (device and
+// driver context handle), so a device reset or a caller-made context gets a
+// fresh lookup instead of a stale address.  Every GPU that loads the library
 // holds the array until the process exits.
 namespace hd {
 
@@ -25,21 +28,50 @@ constexpr size_t kStaticScratchBytes = (size_t)64 << 20;   // 64 MiB
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 static std::mutex g_static_mu;
-static void *g_static_ptr[64] = {nullptr};
+// remembered lookups: (device, context handle) -> address
+struct StaticEntry {
+  int dev;
+  void *ctx;
+  void *ptr;
+};
+static std::vector<StaticEntry> g_static_cache;
+
+// The current driver context handle, through the runtime's driver entry point (the
+// library links the CUDA runtime only); nullptr if it cannot be had.
+static void *current_context() {
+  typedef int (*GetCurrentFn)(void **);
+  static GetCurrentFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<GetCurrentFn>(f);
+  }
+  void *ctx = nullptr;
+  if (!fn || fn(&ctx) != 0) return nullptr;
+  return ctx;
+}
 
 static int static_scratch_ptr(void **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-  if (dev < 0 || dev >= 64) { set_error("device index out of range"); return HD_ERR_INVALID; }
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
-    g_static_ptr[dev] = p;
-  }
-  *out = g_static_ptr[dev];
+  void *ctx = current_context();
+  if (ctx)
+    for (const StaticEntry &se : g_static_cache)
+      if (se.dev == dev && se.ctx == ctx) {
+        *out = se.ptr;
+        return HD_OK;
+      }
+  void *p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress");
+  if (ctx) g_static_cache.push_back({dev, ctx, p});   // without a handle: look up on every call
+  *out = p;
   return HD_OK;
 }
 

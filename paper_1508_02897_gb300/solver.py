@@ -216,13 +216,20 @@ class Server:
 
     def submit(self, c, f, N, npml, omega, nbx, nby, overlap, restart, rtol, max_iters=5000, precision="c64",
                cut_x=None, cut_y=None, arnoldi="auto", symmetric=True, reorth="selective", tcore=False,
-               smoothing=False):
-        """c: float64 [n][n], f: complex128 [nrhs][n][n] host arrays.  Returns a ticket."""
+               smoothing=False, out=None):
+        """c: float64 [n][n], f: complex128 [nrhs][n][n] host arrays (pinned memory, e.g. numpy
+        views of pinned torch tensors, makes the copies direct); out: optional host array for
+        the solutions, shaped like f.  Returns a ticket."""
         c = np.ascontiguousarray(c, dtype=np.float64)
         f = np.ascontiguousarray(f, dtype=np.complex128)
         if f.ndim == 2:
             f = f[None]
-        x = np.empty_like(f)
+        if out is not None:
+            x = out.reshape(f.shape)
+            if x.dtype != np.complex128 or not x.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be a contiguous complex128 array shaped like f")
+        else:
+            x = np.empty_like(f)
         prec = {"c64": B.HD_C64, "c64h": B.HD_C64_H, "c128": B.HD_C128}[precision]
         mode = arnoldi if arnoldi != "auto" else ("ds" if prec != B.HD_C128 else "fp64")
         t = B.hd_submit(self.srv, N, N, npml, 1.0 / N, omega, c.ctypes.data, f.ctypes.data, f.shape[0],
