@@ -83,6 +83,8 @@ def parse():
     p.add_argument("--nrhs", type=int, default=None, help="sources per solve (batching config: 64)")
     p.add_argument("--group", type=int, default=64, help="sources solved together in lockstep (default: all of the batching workload)")
     p.add_argument("--single-sample", type=int, default=2, help="batching: sources also solved one at a time")
+    p.add_argument("--no-legs", dest="legs", action="store_false",
+                   help="precision config: skip the batching and serving sub-results")
     return p.parse_args()
 
 
@@ -263,7 +265,7 @@ def run_ours(args, world, rank, local):
     if args.storage == "auto":   # tensor cores pay once a lockstep group is wide enough
         args.storage = "tc" if group >= 8 and args.precision == "c64" else "sym"
 
-    def one_solve(precision, profile, f=None, grp=None, storage=None, arnoldi=None):
+    def one_solve(precision, profile, f=None, grp=None, storage=None, arnoldi=None, graphs=False):
         f = f_d if f is None else f
         grp = group if grp is None else grp
         storage = storage or args.storage
@@ -280,7 +282,7 @@ def run_ours(args, world, rank, local):
         for g0 in range(0, f.shape[0], grp):
             b = s.rhs(f[g0:g0 + grp])
             x, st = s.solve(b, restart=wl.restart, rtol=wl.rtol, max_iters=args.max_iters,
-                            arnoldi=arnoldi, reorth=args.reorth,
+                            arnoldi=arnoldi, reorth=args.reorth, graphs=graphs,
                             precond_steps=args.precond_steps)
             sts.extend(st)
         tm = s.timers(reset=True)
@@ -484,11 +486,93 @@ def run_ours(args, world, rank, local):
                       "path": "C ABI hd_submit/hd_poll with pinned host buffers",
                       "iters": [x["iters"] for x in est], "converged": all(x["converged"] == 1 for x in est)}
 
+    if world == 1 and args.legs and args.config == "precision":
+        out["batching"] = batching_leg(args, dev, local)
+        out["serving"] = serving_legs(args, world, rank, local)
+
     if rank == 0 and not args.no_cpu_baseline:
         it_ref = int(round(statistics.mean(iters)))
         out["cpu_baseline"] = cpu_baseline(wl, it_ref, args.cpu_sample_boxes, "GPU FGMRES iteration count",
                                            nrhs=wl.nrhs)
     return out
+
+
+def batching_leg(args, dev, local, warmup=1, steps=2):
+    """The batching configuration: 1984^2 random medium, 16 x 16 boxes (edge boxes 96^2
+    owned), 64 Gaussian sources sharing one factorisation, solved as one lockstep group with
+    the tensor-core substitution and every Arnoldi step replayed from a CUDA graph.  One step
+    = factorisation + the 64-source solve; solves/s counts sources."""
+    import copy
+    import torch
+    from paper_1508_02897_gb300.solver import HelmholtzDDM
+    a = copy.copy(args)
+    a.config, a.nrhs = "batching", 64
+    wl = workload(a, 0)
+    c_d = torch.from_numpy(wl.c).to(dev)
+    f_d = torch.from_numpy(wl.f).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(profile):
+        s = HelmholtzDDM(wl.N, wl.npml, wl.omega, c_d, wl.nbx, wl.nby, wl.overlap, precision="c64",
+                         cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev), symmetric=False, tcore=True)
+        s.set_profiling(profile)
+        s.factor()
+        b = s.rhs(f_d)
+        _, st = s.solve(b, restart=wl.restart, rtol=wl.rtol, max_iters=args.max_iters, reorth=args.reorth,
+                        graphs=True)
+        tm = s.timers(reset=True)
+        s.close()
+        return st, tm
+
+    for _ in range(warmup):
+        step(False)
+    torch.cuda.synchronize(dev)
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    stats, tms = [], []
+    for k in range(steps):
+        st, tm = step(True)
+        ev[k + 1].record(stream)
+        stats.extend(st)
+        tms.append(tm)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    tot = sum(step_ms) / 1e3
+    its = [x["iters"] for x in stats]
+    cls = tms[0].keys()
+    return {"workload": describe(wl, "c64"), "value": steps * wl.nrhs / tot, "unit": "solves/s",
+            "steps": steps, "warmup": warmup, "ms_per_step": tot * 1e3 / steps,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+            "sources_per_step": wl.nrhs, "lockstep_group": wl.nrhs, "cuda_graphs": True,
+            "factor_storage": "TF32 real/imag planes, tensor-core substitution",
+            "iters": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its))},
+            "relres_true_max": float(max(x["relres_true"] for x in stats)),
+            "converged": all(x["converged"] == 1 for x in stats),
+            "breakdown_ms_per_step": {c: sum(t[c][0] for t in tms) / steps for c in cls},
+            "gpu_launches_per_step": int(sum(sum(t[c][1] for c in cls) for t in tms) / steps), "clocks": clk}
+
+
+def serving_legs(args, world, rank, local):
+    """The serving configuration through hd_submit/hd_poll: the configured mix (grids
+    256..4096, three media, 1..16 sources) at 20 requests/s for a capped number of
+    requests (the offered rate overloads one GPU), and a stable point at 0.25 requests/s."""
+    import copy
+    legs = {}
+    for name, rate, nreq in (("offered_20_per_s", 20.0, 24), ("stable_0.25_per_s", 0.25, 6)):
+        a = copy.copy(args)
+        a.rate, a.window, a.max_requests = rate, max(10.0, 2.0 * nreq / rate), nreq
+        a.grids = "256,512,1024,2048,4096"
+        clocks = Clocks(local)
+        clocks.start()
+        r = run_serving(a, world, rank, local)
+        r["clocks"] = clocks.stop()
+        legs[name] = {k: r[k] for k in ("value", "unit", "requests", "offered_req_per_s", "completed_req_per_s",
+                                        "total_solves", "converged_solves", "latency_s", "unknown_iters_per_s",
+                                        "wall_s", "peak_running", "peak_bytes_in_use", "clocks")}
+    return legs
 
 
 def _dtype_label(args):
@@ -563,12 +647,15 @@ def run_serving(args, world, rank, local):
     trace = W.poisson_trace(4 + 101 * rank, args.rate, args.window, grids=grids)
     if args.max_requests:
         trace = trace[:args.max_requests]
-    reqs = []
-    for q in trace:
+    from concurrent.futures import ThreadPoolExecutor
+
+    def make(q):   # the requests' inputs, prepared on the host before the clock starts
         N = q["N"]
-        wl = W.make_workload("tiny", N=N, nb=max(1, N // 128), medium=q["medium"], seed=q["seed"], nrhs=q["nrhs"],
-                             restart=_serving_restart(max(1, N // 128)), rtol=1e-6)
-        reqs.append((q["t"], wl))
+        return q["t"], W.make_workload("tiny", N=N, nb=max(1, N // 128), medium=q["medium"], seed=q["seed"],
+                                       nrhs=q["nrhs"], restart=_serving_restart(max(1, N // 128)), rtol=1e-6)
+
+    with ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
+        reqs = list(ex.map(make, trace))
     srv = Server(hbm_budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots, device=local)
     barrier(world)
     t0 = time.perf_counter()
@@ -754,7 +841,7 @@ def run_study(args, world, rank, local):
         ov, npml = (int(v) for v in pair.split(":"))
         a = copy.copy(args)
         a.overlap, a.npml, a.study = ov, npml, None
-        a.fp64_steps, a.e2e_steps, a.no_cpu_baseline, a.single_sample = 0, 0, True, 0
+        a.fp64_steps, a.e2e_steps, a.no_cpu_baseline, a.single_sample, a.legs = 0, 0, True, 0, False
         out = run_ours(a, world, rank, local)
         if rank == 0:
             row = {"overlap": ov, "npml": npml, "iters": out["iters"], "ms_per_solve": out["ms_per_step"],
