@@ -54,7 +54,7 @@ def parse():
     p.add_argument("--max-requests", type=int, default=0, help="serving: cap on the number of requests (0: none)")
     p.add_argument("--slots", type=int, default=4)
     p.add_argument("--budget-gb", type=float, default=160.0)
-    p.add_argument("--precision", default="c64", choices=("c64", "c64h", "c128"))
+    p.add_argument("--precision", default="c64", choices=("c64", "c64h", "c64b", "c128"))
     p.add_argument("--restart", type=int, default=None)
     p.add_argument("--rtol", type=float, default=None)
     p.add_argument("--max-iters", type=int, default=3000)
@@ -321,7 +321,7 @@ def run_ours(args, world, rank, local):
     cls_n = {c: sum(t[c][1] for t in timers) for c in classes}
     launches = int(sum(cls_n.values()))
     cs = 16 if args.precision == "c128" else 8                       # staging (compute) entry
-    fs = {"c128": 16, "c64": 8, "c64h": 4}[args.precision]          # stored factor entry
+    fs = {"c128": 16, "c64": 8, "c64h": 4, "c64b": 4}[args.precision]   # stored factor entry
     sym = args.storage
     sb = subst_bytes(wl, cs, group, fs, sym)
     sub_avg_ms = cls_ms["subst"] / max(cls_n["subst"], 1)
@@ -577,7 +577,8 @@ def serving_legs(args, world, rank, local):
 
 def _dtype_label(args):
     """Arithmetic of the path: local factors and substitutions, Gram-Schmidt, outer loop."""
-    fac = {"c64": "c64 factors", "c64h": "c64 factors stored c32 (FP16 pairs)", "c128": "c128 factors"}[args.precision]
+    fac = {"c64": "c64 factors", "c64h": "c64 factors stored c32 (FP16 pairs)",
+           "c64b": "c64 factors stored c32 (BF16 pairs)", "c128": "c128 factors"}[args.precision]
     if args.storage == "tc":
         fac += " (TF32 storage, tensor-core substitution)"
     ds = args.arnoldi == "ds" or (args.arnoldi == "auto" and args.precision != "c128")
@@ -619,7 +620,7 @@ def _profile_traffic(wl, args):
                 or d.get("storage", "full") != args.storage):
             return None
         cs = 16 if args.precision == "c128" else 8
-        fs = {"c128": 16, "c64": 8, "c64h": 4}[args.precision]
+        fs = {"c128": 16, "c64": 8, "c64h": 4, "c64b": 4}[args.precision]
         return d["dram_bytes_per_launch"] * subst_bytes(wl, cs, 1, fs, sym) / d["algorithmic_bytes_per_launch"]
     except Exception:
         return None

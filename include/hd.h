@@ -50,9 +50,11 @@ typedef enum {
 typedef enum {
   HD_C128 = 0,  /* local factors and substitutions in complex FP64              */
   HD_C64 = 1,   /* local factors and substitutions in complex FP32, FP64 outside */
-  HD_C64_H = 2  /* as HD_C64, but the stored S_j^{-1} are complex FP16 (half the
+  HD_C64_H = 2, /* as HD_C64, but the stored S_j^{-1} are complex FP16 (half the
                    bytes streamed by every preconditioner application); the
                    factorisation recursion itself stays FP32                     */
+  HD_C64_B = 3  /* as HD_C64_H with complex BF16 storage: the same halved bytes,
+                   an 8-bit mantissa instead of 11 but FP32's exponent range     */
 } hd_precision;
 
 /* Flag OR-ed into the precision of hd_setup_medium: store only the upper

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(HERE, "libhd.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "hd.h")
 
 HD_OK, HD_ERR_INVALID, HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_NOT_CONVERGED, HD_ERR_NUMERIC, HD_ERR_TIMEOUT, HD_PENDING = range(8)
-HD_C128, HD_C64, HD_C64_H = 0, 1, 2
+HD_C128, HD_C64, HD_C64_H, HD_C64_B = 0, 1, 2, 3
 HD_SYMMETRIC = 0x100
 HD_TCORE = 0x200
 HD_SMOOTH = 0x400

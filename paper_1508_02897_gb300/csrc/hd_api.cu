@@ -152,7 +152,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   if (dec->nbx < 1 || dec->nby < 1 || dec->overlap < 0 || dec->nbx > grid->nx || dec->nby > grid->ny)
     return invalid("hd_setup_medium: bad decomposition");
   const int base_prec = precision & 0xff;
-  if ((base_prec != HD_C128 && base_prec != HD_C64 && base_prec != HD_C64_H) ||
+  if ((base_prec != HD_C128 && base_prec != HD_C64 && base_prec != HD_C64_H && base_prec != HD_C64_B) ||
       (precision & ~(0xff | HD_SYMMETRIC | HD_TCORE | HD_SMOOTH)))
     return invalid("hd_setup_medium: bad precision");
   if ((precision & HD_TCORE) && (base_prec != HD_C64 || (precision & HD_SYMMETRIC)))

@@ -407,6 +407,7 @@ static cudaError_t launch_factor_simt(hd_ctx *ctx, void *factor, void *work, con
   return ctx->tc                  ? launch_factor_rs<float, float2, LAY_TC>(ctx, factor, work, only, st)
          : ctx->prec == HD_C64   ? launch_factor_r<float, float2>(ctx, factor, work, only, st)
          : ctx->prec == HD_C64_H ? launch_factor_r<float, __half2>(ctx, factor, work, only, st)
+         : ctx->prec == HD_C64_B ? launch_factor_r<float, __nv_bfloat162>(ctx, factor, work, only, st)
                                  : launch_factor_r<double, double2>(ctx, factor, work, only, st);
 }
 

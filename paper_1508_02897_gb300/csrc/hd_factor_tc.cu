@@ -631,6 +631,9 @@ cudaError_t launch_factor_tc(hd_ctx *ctx, void *factor, cudaStream_t st) {
   if (ctx->tc) return launch_tc<float2, LAY_TC>(ctx, factor, tau2, st);
   if (ctx->prec == HD_C64)
     return ctx->sym ? launch_tc<float2, LAY_SYM>(ctx, factor, tau2, st) : launch_tc<float2, LAY_FULL>(ctx, factor, tau2, st);
+  if (ctx->prec == HD_C64_B)
+    return ctx->sym ? launch_tc<__nv_bfloat162, LAY_SYM>(ctx, factor, tau2, st)
+                    : launch_tc<__nv_bfloat162, LAY_FULL>(ctx, factor, tau2, st);
   return ctx->sym ? launch_tc<__half2, LAY_SYM>(ctx, factor, tau2, st) : launch_tc<__half2, LAY_FULL>(ctx, factor, tau2, st);
 }
 

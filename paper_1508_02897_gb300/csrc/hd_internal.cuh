@@ -1,6 +1,7 @@
 // Internal declarations shared by the translation units of libhd.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -126,11 +127,17 @@ __host__ __device__ __forceinline__ double2 to_c(double2 z, double2) { return z;
 __host__ __device__ __forceinline__ double2 to_d(float2 z) { return make_double2(z.x, z.y); }
 __host__ __device__ __forceinline__ double2 to_d(double2 z) { return z; }
 
-// Stored factor entries: the compute type itself, or complex FP16 for FP32 math.
+// Stored factor entries: the compute type itself, or complex FP16 / BF16 for FP32 math.
 template <typename S, typename T> __device__ __forceinline__ S store_c(T v) { return v; }
 template <> __device__ __forceinline__ __half2 store_c<__half2, float2>(float2 v) { return __float22half2_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat162 store_c<__nv_bfloat162, float2>(float2 v) {
+  return __float22bfloat162_rn(v);
+}
 template <typename T, typename S> __device__ __forceinline__ T load_c(S v) { return v; }
 template <> __device__ __forceinline__ float2 load_c<float2, __half2>(__half2 v) { return __half22float2(v); }
+template <> __device__ __forceinline__ float2 load_c<float2, __nv_bfloat162>(__nv_bfloat162 v) {
+  return __bfloat1622float2(v);
+}
 
 // Bytes of one stored factor entry and of one compute (staging / working) entry.
 inline size_t store_bytes(int prec) { return prec == HD_C128 ? 16 : (prec == HD_C64 ? 8 : 4); }

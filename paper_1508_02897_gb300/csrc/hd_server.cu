@@ -233,7 +233,8 @@ int hd_submit(hd_server *s, const hd_grid *grid, const hd_decomp *dec, const dou
               int32_t nrhs, int32_t precision, const hd_gmres_opts *opts, void *x_host, uint64_t *ticket) {
   if (!s || !grid || !dec || !c_host || !f_host || !opts || !x_host || !ticket || nrhs < 1 || opts->restart < 1 ||
       opts->restart > HD_MAX_RESTART ||
-      ((precision & 0xff) != HD_C64 && (precision & 0xff) != HD_C128 && (precision & 0xff) != HD_C64_H) ||
+      ((precision & 0xff) != HD_C64 && (precision & 0xff) != HD_C128 && (precision & 0xff) != HD_C64_H &&
+       (precision & 0xff) != HD_C64_B) ||
       (precision & ~(0xff | HD_SYMMETRIC | HD_TCORE | HD_SMOOTH)) ||
       ((precision & HD_TCORE) && ((precision & 0xff) != HD_C64 || (precision & HD_SYMMETRIC)))) {
     set_error("hd_submit: bad argument");

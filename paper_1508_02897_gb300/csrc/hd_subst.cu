@@ -81,7 +81,7 @@ template <int CT, int NA> __device__ __forceinline__ int out_index(int t, int e)
   return NA == 2 ? 2 * t + e : t + CT * e;
 }
 
-// Two adjacent stored entries p[0], p[1] (16-byte aligned for float2 / 8 for half2).
+// Two adjacent stored entries p[0], p[1] (16-byte aligned for float2 / 8 for half2 and bfloat162).
 template <typename T, typename S> __device__ __forceinline__ void load_pair(const S *p, T &v0, T &v1) {
   v0 = load_c<T>(p[0]);
   v1 = load_c<T>(p[1]);
@@ -95,6 +95,12 @@ template <> __device__ __forceinline__ void load_pair<float2, __half2>(const __h
   const uint2 q = *reinterpret_cast<const uint2 *>(p);
   v0 = __half22float2(*reinterpret_cast<const __half2 *>(&q.x));
   v1 = __half22float2(*reinterpret_cast<const __half2 *>(&q.y));
+}
+template <>
+__device__ __forceinline__ void load_pair<float2, __nv_bfloat162>(const __nv_bfloat162 *p, float2 &v0, float2 &v1) {
+  const uint2 q = *reinterpret_cast<const uint2 *>(p);
+  v0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.x));
+  v1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&q.y));
 }
 
 // Shared memory layout: ring [NS][CH*ldmax] (stored type S) | vs [NR][ldmax] (compute type T) |
@@ -724,6 +730,7 @@ int run_apply(hd_ctx *ctx, const double2 *r, int64_t rs, double2 *z, int64_t zs,
               cudaStream_t st) {
   cudaError_t e = ctx->prec == HD_C64    ? launch_apply_r<float, float2>(ctx, r, rs, z, zs, nrhs, staging, st)
                   : ctx->prec == HD_C64_H ? launch_apply_r<float, __half2>(ctx, r, rs, z, zs, nrhs, staging, st)
+                  : ctx->prec == HD_C64_B ? launch_apply_r<float, __nv_bfloat162>(ctx, r, rs, z, zs, nrhs, staging, st)
                                           : launch_apply_r<double, double2>(ctx, r, rs, z, zs, nrhs, staging, st);
   if (e != cudaSuccess) return cuda_fail(e, "preconditioner launch");
   return HD_OK;

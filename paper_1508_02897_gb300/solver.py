@@ -45,7 +45,7 @@ class HelmholtzDDM:
         self.N, self.npml, self.n = N, npml, N + 2 * npml
         self.device = torch.device(device)
         self.stream = stream
-        self.prec = {"c64": B.HD_C64, "c64h": B.HD_C64_H, "c128": B.HD_C128}[precision]
+        self.prec = {"c64": B.HD_C64, "c64h": B.HD_C64_H, "c64b": B.HD_C64_B, "c128": B.HD_C128}[precision]
         c_t = torch.as_tensor(np.asarray(c, dtype=np.float64) if not torch.is_tensor(c) else c,
                               dtype=torch.float64).to(self.device).contiguous()
         assert c_t.shape == (self.n, self.n), f"velocity must be {(self.n, self.n)}"
@@ -230,7 +230,7 @@ class Server:
                 raise ValueError("out must be a contiguous complex128 array shaped like f")
         else:
             x = np.empty_like(f)
-        prec = {"c64": B.HD_C64, "c64h": B.HD_C64_H, "c128": B.HD_C128}[precision]
+        prec = {"c64": B.HD_C64, "c64h": B.HD_C64_H, "c64b": B.HD_C64_B, "c128": B.HD_C128}[precision]
         mode = arnoldi if arnoldi != "auto" else ("ds" if prec != B.HD_C128 else "fp64")
         t = B.hd_submit(self.srv, N, N, npml, 1.0 / N, omega, c.ctypes.data, f.ctypes.data, f.shape[0],
                         prec | _storage_flag(prec, symmetric, tcore, smoothing),

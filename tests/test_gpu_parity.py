@@ -6,7 +6,10 @@ rounding times the local condition number: matvec 1e-13, preconditioner 1e-10
 relative L2, FGMRES iterate after a fixed number of steps 1e-9.  The c64 path
 stores the local factors in complex FP32: preconditioner 2e-4 relative L2
 (FP32 rounding amplified by the local problems' condition number), final
-solution 1e-5 against the FP64 oracle at relative residual 1e-8.
+solution 1e-5 against the FP64 oracle at relative residual 1e-8.  Reduced-precision
+storage of the factors scales that bound by its unit roundoff over FP32's: TF32 and
+FP16 storage (2^-11) 3e-2, BF16 storage (2^-8, eight times coarser) 1.2e-1; the FP64
+outer loop still reaches its tolerance.
 """
 import numpy as np
 import pytest
@@ -74,7 +77,8 @@ def test_matvec_and_rhs(name):
 
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4), ("c64h", 3e-2), ("c128s", 1e-10),
-                                           ("c64s", 2e-4), ("c64hs", 3e-2), ("c64t", 3e-2)])
+                                           ("c64s", 2e-4), ("c64hs", 3e-2), ("c64t", 3e-2), ("c64b", 1.2e-1),
+                                           ("c64bs", 1.2e-1)])
 def test_precond_parity(name, precision, tol):
     _, _, g, _, P = oracle(name)
     s = gpu(name, precision)
@@ -130,7 +134,7 @@ def test_gmres_converged_c128(name, arnoldi, reorth):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("precision", ["c64", "c64h", "c64s", "c64t"])
+@pytest.mark.parametrize("precision", ["c64", "c64h", "c64s", "c64t", "c64bs"])
 def test_gmres_mixed_precision(name, precision):
     """FP32 local factors (stored in FP32, FP16 or TF32), FP64 outer loop: the FP64
     relative residual reaches the tolerance and the solution matches the FP64
