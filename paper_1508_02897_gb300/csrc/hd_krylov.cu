@@ -344,6 +344,7 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
                                                   int scale) {
   extern __shared__ float4 csm[];  // [nk]
   __shared__ double nsm[DT / 32];
+  __shared__ double gsm;
   const int tid = threadIdx.x, r = blockIdx.y;
   if ((skip && skip[r]) || (live && !live[r])) return;
   const double2 *coef = coef_all + (int64_t)r * ldc;
@@ -352,7 +353,11 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
   const double2 *base = base_all + (int64_t)r * ldy;
   double2 *y = y_all + (int64_t)r * ldy;
   float4 *vout = vout_all + (int64_t)r * ldvr;
-  const double g = scale ? lazy_gamma(coef[nk].x) : 1.0;
+  // the output scale once per block (an FP64 square root and division)
+  if (tid == 0) gsm = scale ? lazy_gamma(coef[nk].x) : 1.0;
+  __syncthreads();
+  const double g = gsm;
+  const float2 gds = ds_split(g);
   for (int k = tid; k < nk; k += DT) {
     const double2 c0 = coef[k];
     const double s2 = sc[k] * sc[k] * g;
@@ -395,10 +400,15 @@ __global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, 
     for (int e = 0; e < E; ++e) {
       int64_t i = b0 + (int64_t)DT * (half * E + e);
       if (i < n) {
-        // y = base - acc in double-single, then one FP64 add per component
+        // y = g base - acc in double-single (g base as a double-single product: no FP64
+        // multiply), then one FP64 add per component
         const double2 bv = base[i];
-        const float2 br = ds_split(g * bv.x), bi = ds_split(g * bv.y);
-        float oh = br.x, ol = br.y, qh = bi.x, ql = bi.y;
+        const float2 br = ds_split(bv.x), bi = ds_split(bv.y);
+        float oh = 0.f, ol = 0.f, qh = 0.f, ql = 0.f;
+        ds_mac(oh, ol, gds.x, gds.y, br.x, br.y);
+        ds_mac(qh, ql, gds.x, gds.y, bi.x, bi.y);
+        ds_renorm(oh, ol);
+        ds_renorm(qh, ql);
         ds_add(oh, ol, -rh[e], -rl[e]);
         ds_add(qh, ql, -ih[e], -il[e]);
         y[i] = make_double2(ds_to_d(oh, ol), ds_to_d(qh, ql));
