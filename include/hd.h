@@ -293,6 +293,40 @@ int hd_gmres_solve(hd_ctx *ctx, const void *b_dev, void *x_dev, int32_t nrhs, co
                    void *krylov_dev, size_t krylov_bytes, void *scratch_dev, size_t scratch_bytes,
                    hd_gmres_stats *stats_host, void *stream);
 
+/* Largest block (right-hand sides sharing one Krylov space) of hd_block_gmres_solve. */
+#define HD_MAX_BLOCK 128
+
+/* Bytes of the block solver's workspaces for p right-hand sides and `restart` block
+ * steps per cycle: krylov_bytes holds the block bases V ((restart+1) p vectors) and
+ * Z (restart p), one more block and the Gram reduction buffers; scratch_bytes the
+ * substitution staging of p right-hand sides (or the factorisation working matrix,
+ * whichever is larger).  Outputs may be NULL; HD_ERR_INVALID for p outside
+ * 1 .. HD_MAX_BLOCK or restart outside 1 .. HD_MAX_RESTART. */
+int hd_query_block_workspace(const hd_ctx *ctx, int32_t p, int32_t restart, size_t *krylov_bytes,
+                             size_t *scratch_bytes);
+
+/* Block flexible GMRES (Sec. 3's GMRES taken to p sources sharing one Krylov space;
+ * the block method of Saad, Iterative Methods for Sparse Linear Systems, Sec. 6.12,
+ * flexible as in Sec. 9.4): per cycle R = B - A X = V_0 S (thin QR); block step j
+ * applies the one-step preconditioner of Eq. (pc) to the p columns of V_j in one
+ * launch (Z_j), W = A Z_j, block classical Gram-Schmidt twice (H_ij = V_i^H W for all
+ * i <= j from the same W, W -= sum V_i H_ij), W = V_{j+1} H_{j+1,j} by Cholesky QR done
+ * twice; the least squares min || E_1 S - Hbar Y ||_F is updated on the host (FP64
+ * Householder QR) and gives each column's residual estimate.  The cycle ends when every
+ * estimate is <= rtol, at the restart, or when a new block loses a direction; then
+ * X += [Z_0 .. Z_k] Y and the FP64 true residual decides.  All of it runs in FP64 but the
+ * preconditioner, which uses the context's precision.  b_dev, x_dev: complex128
+ * [p][NY][NX]; x_dev is the output (and the start when opts->use_x0).  opts->restart
+ * counts block steps per cycle, opts->max_iters block steps in all; arnoldi, graphs
+ * and reorth are ignored, precond_steps must be 0 or 1.  Blocking; stats_host[p]: iters
+ * = block steps (each one preconditioner launch for the p columns), converged and
+ * relres_true per column.  HD_ERR_NUMERIC if the first residual block is rank deficient
+ * (dependent sources: solve them separately), HD_ERR_NOT_CONVERGED if a column missed
+ * rtol within max_iters. */
+int hd_block_gmres_solve(hd_ctx *ctx, const void *b_dev, void *x_dev, int32_t p, const hd_gmres_opts *opts,
+                         void *krylov_dev, size_t krylov_bytes, void *scratch_dev, size_t scratch_bytes,
+                         hd_gmres_stats *stats_host, void *stream);
+
 /* Autotuner (no counterpart in the paper): times hd_apply_precond's
  * substitution kernel for each candidate launch shape (96, 128, 192 or 256
  * consumer threads per CTA, 2 to 32 ring stages that fit shared memory) on r_dev ->

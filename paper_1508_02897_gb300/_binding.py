@@ -23,6 +23,7 @@ HD_SMOOTH = 0x400
 HD_ARNOLDI_FP64, HD_ARNOLDI_DS = 0, 1
 HD_FACTOR_AUTO, HD_FACTOR_SIMT, HD_FACTOR_TCORE = 0, 1, 2
 HD_MAX_RESTART = 256
+HD_MAX_BLOCK = 128
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID", 2: "HD_ERR_OOM", 3: "HD_ERR_CUDA", 4: "HD_ERR_NOT_CONVERGED",
                 5: "HD_ERR_NUMERIC", 6: "HD_ERR_TIMEOUT", 7: "HD_PENDING"}
 TIMER_CLASSES = ("factor", "subst", "gather", "matvec", "arnoldi", "other")
@@ -92,6 +93,9 @@ _SIGS = {
     "hd_gmres_solve": [_P, _P, _P, ct.c_int32, ct.POINTER(hd_gmres_opts), _P, ct.c_size_t, _P, ct.c_size_t,
                        ct.POINTER(hd_gmres_stats), _P],
     "hd_apply_precond_noalloc": [_P, _P, _P, ct.c_int32, _P],
+    "hd_query_block_workspace": [_P, ct.c_int32, ct.c_int32, ct.POINTER(ct.c_size_t), ct.POINTER(ct.c_size_t)],
+    "hd_block_gmres_solve": [_P, _P, _P, ct.c_int32, ct.POINTER(hd_gmres_opts), _P, ct.c_size_t, _P, ct.c_size_t,
+                             ct.POINTER(hd_gmres_stats), _P],
     "hd_autotune": [_P, _P, _P, _P, ct.c_size_t, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_int32),
                     ct.POINTER(ct.c_float), _P],
     "hd_set_profiling": [_P, ct.c_int32],
@@ -210,6 +214,23 @@ def hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, restart, max_iters, rtol, krylov_ptr
     allow = () if raise_on_not_converged else (HD_ERR_NOT_CONVERGED,)
     rc = _check("hd_gmres_solve", lib().hd_gmres_solve(ctx, b_ptr, x_ptr, nrhs, ct.byref(o), krylov_ptr, krylov_bytes,
                                                        scratch_ptr, scratch_bytes, st, stream), allow)
+    return rc, [s.as_dict() for s in st]
+
+
+def hd_query_block_workspace(ctx, p, restart):
+    """(krylov bytes, scratch bytes) of the block solver for p right-hand sides."""
+    k, s = ct.c_size_t(), ct.c_size_t()
+    _check("hd_query_block_workspace", lib().hd_query_block_workspace(ctx, p, restart, ct.byref(k), ct.byref(s)))
+    return k.value, s.value
+
+
+def hd_block_gmres_solve(ctx, b_ptr, x_ptr, p, restart, max_iters, rtol, krylov_ptr, krylov_bytes, scratch_ptr,
+                         scratch_bytes, stream, use_x0=0):
+    o = hd_gmres_opts(restart, max_iters, rtol, use_x0, HD_ARNOLDI_FP64, 0, 0, 1)
+    st = (hd_gmres_stats * p)()
+    rc = _check("hd_block_gmres_solve", lib().hd_block_gmres_solve(ctx, b_ptr, x_ptr, p, ct.byref(o), krylov_ptr,
+                                                                   krylov_bytes, scratch_ptr, scratch_bytes, st,
+                                                                   stream), (HD_ERR_NOT_CONVERGED,))
     return rc, [s.as_dict() for s in st]
 
 

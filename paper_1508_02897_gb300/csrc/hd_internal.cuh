@@ -318,6 +318,10 @@ int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cud
 int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const hd_gmres_opts *o, void *kws,
                     void *scratch, hd_gmres_stats *stats, cudaStream_t st);
 size_t factor_smem_bytes(int prec, int max_m);
+// Block flexible GMRES (hd_block.cu)
+size_t block_krylov_bytes(int64_t n, int restart, int p);
+int run_block_gmres(hd_ctx *ctx, const double2 *b, double2 *x, int p, const hd_gmres_opts *o, void *kws,
+                    void *scratch, hd_gmres_stats *stats, cudaStream_t st);
 // Tensor-core factorisation (hd_factor_tc.cu): complex FP32 arithmetic, boxes up to 192 wide.
 bool factor_tc_supported(const hd_ctx *ctx);
 cudaError_t launch_factor_tc(hd_ctx *ctx, void *factor, cudaStream_t st);

@@ -162,6 +162,22 @@ class HelmholtzDDM:
                                      precond_steps=int(precond_steps))
         return x, stats
 
+    def block_solve(self, b, restart: int = 10, rtol: float = 1e-8, max_iters: int = 1000, x0=None):
+        """Block flexible GMRES (hd_block_gmres_solve) of A X = B for the p sources in b
+        ([p, n, n]) sharing one Krylov space; `restart` and `max_iters` count block steps."""
+        b, p = self._vec(b)
+        x = self._vec(x0)[0].clone() if x0 is not None else torch.empty_like(b)
+        kb, sb = B.hd_query_block_workspace(self.ctx, p, restart)
+        with torch.cuda.stream(self.stream):
+            kws = torch.empty(kb, dtype=torch.uint8, device=self.device)
+            if sb > self.scratch_bytes:
+                self.scratch = torch.empty(sb, dtype=torch.uint8, device=self.device)
+                self.scratch_bytes = sb
+        rc, stats = B.hd_block_gmres_solve(self.ctx, b.data_ptr(), x.data_ptr(), p, restart, max_iters, rtol,
+                                           kws.data_ptr(), kb, self.scratch.data_ptr(), self.scratch_bytes,
+                                           self._st(), use_x0=int(x0 is not None))
+        return x, stats
+
     def _arnoldi(self, mode: str) -> int:
         if mode == "auto":
             mode = "ds" if self.prec != B.HD_C128 else "fp64"

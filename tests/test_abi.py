@@ -68,3 +68,20 @@ def test_restart_bound_is_enforced_without_gpu():
         assert L.hd_gmres_solve(p, p, p, 1, ctypes.byref(o), p, 1 << 20, p, 1 << 20, st, None) == B.HD_ERR_INVALID
         assert "bad options" in B.hd_last_error()
 
+
+
+def test_block_solver_validates_without_gpu():
+    """The block solver refuses bad block sizes, restarts and the multi-step preconditioner
+    before any pointer is used or any CUDA call is made."""
+    from paper_1508_02897_gb300 import _binding as B
+    L = B.lib()
+    p_ = ctypes.c_void_p(16)
+    kb, sb = ctypes.c_size_t(), ctypes.c_size_t()
+    for blk, restart in ((0, 5), (B.HD_MAX_BLOCK + 1, 5), (3, 0), (3, B.HD_MAX_RESTART + 1)):
+        assert L.hd_query_block_workspace(p_, blk, restart, ctypes.byref(kb), ctypes.byref(sb)) == B.HD_ERR_INVALID
+    st = (B.hd_gmres_stats * 3)()
+    o = B.hd_gmres_opts(5, 100, 1e-6, 0, B.HD_ARNOLDI_FP64, 0, 0, 2)   # two preconditioner steps
+    assert L.hd_block_gmres_solve(p_, p_, p_, 3, ctypes.byref(o), p_, 1 << 20, p_, 1 << 20, st, None) == B.HD_ERR_INVALID
+    o = B.hd_gmres_opts(5, 100, 1e-6, 0, B.HD_ARNOLDI_FP64, 0, 0, 1)
+    assert L.hd_block_gmres_solve(None, p_, p_, 3, ctypes.byref(o), p_, 1 << 20, p_, 1 << 20, st, None) == B.HD_ERR_INVALID
+    assert L.hd_block_gmres_solve(p_, p_, p_, 0, ctypes.byref(o), p_, 1 << 20, p_, 1 << 20, st, None) == B.HD_ERR_INVALID
