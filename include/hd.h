@@ -73,6 +73,16 @@ typedef enum {
  * entry.  The factorisation itself stays FP32; only the stored copy is TF32. */
 #define HD_TCORE 0x200
 
+/* Flag OR-ed into HD_C64 | HD_TCORE: keep FP32-grade products on the tensor cores.
+ * Every stored entry x of S_j^{-1} becomes a pair of TF32 numbers (x_hi = x rounded
+ * to TF32, x_lo = the rest rounded to TF32, |x - x_hi - x_lo| <= 2^-22 |x|), the
+ * right-hand sides are split the same way, and each substitution step takes the
+ * products hi*hi + lo*hi + hi*lo (+ lo*lo) with FP32 accumulation, for groups of 32
+ * right-hand sides per CTA: the accuracy of the FP32 substitution at the factor bytes
+ * per right-hand side of the TF32 storage (16 bytes per entry, read once per 32).
+ * Boxes up to 176 cells wide (hd_setup_medium returns HD_ERR_INVALID otherwise). */
+#define HD_TF32X3 0x800
+
 /* Flag OR-ed into any precision: weight every local solution by the smoothing
  * function beta_ij of the Remark after Eq. (pc) before the sum of Eq. (pc)
  * (beta = 1 on the owned cells, a C^2 step t^3 (10 - 15 t + 6 t^2) of the distance

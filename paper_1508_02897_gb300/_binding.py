@@ -20,6 +20,7 @@ HD_C128, HD_C64, HD_C64_H, HD_C64_B = 0, 1, 2, 3
 HD_SYMMETRIC = 0x100
 HD_TCORE = 0x200
 HD_SMOOTH = 0x400
+HD_TF32X3 = 0x800
 HD_ARNOLDI_FP64, HD_ARNOLDI_DS = 0, 1
 HD_FACTOR_AUTO, HD_FACTOR_SIMT, HD_FACTOR_TCORE = 0, 1, 2
 HD_MAX_RESTART = 256

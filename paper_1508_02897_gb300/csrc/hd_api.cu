@@ -153,8 +153,10 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
     return invalid("hd_setup_medium: bad decomposition");
   const int base_prec = precision & 0xff;
   if ((base_prec != HD_C128 && base_prec != HD_C64 && base_prec != HD_C64_H && base_prec != HD_C64_B) ||
-      (precision & ~(0xff | HD_SYMMETRIC | HD_TCORE | HD_SMOOTH)))
+      (precision & ~(0xff | HD_SYMMETRIC | HD_TCORE | HD_TF32X3 | HD_SMOOTH)))
     return invalid("hd_setup_medium: bad precision");
+  if ((precision & HD_TF32X3) && !(precision & HD_TCORE))
+    return invalid("hd_setup_medium: HD_TF32X3 is a variant of HD_TCORE");
   if ((precision & HD_TCORE) && (base_prec != HD_C64 || (precision & HD_SYMMETRIC)))
     return invalid("hd_setup_medium: HD_TCORE needs HD_C64 and excludes HD_SYMMETRIC");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -166,6 +168,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   c->prec = base_prec;
   c->sym = (precision & HD_SYMMETRIC) != 0;
   c->tc = (precision & HD_TCORE) != 0;
+  c->tc3 = (precision & HD_TF32X3) != 0;
   c->smooth = (precision & HD_SMOOTH) != 0;
   c->stream = st;
   c->nbx = dec->nbx; c->nby = dec->nby; c->overlap = dec->overlap; c->own_global_pml = dec->own_global_pml ? 1 : 0;
@@ -191,7 +194,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
       const int64_t mp8 = (s.ex + 7) & ~7;
       s.foff = foff;
       foff += c->sym ? (int64_t)s.ey * (mt * (mt + 1) / 2) * 256
-                     : (c->tc ? (int64_t)s.ey * mp8 * mp8 : (int64_t)s.ey * s.ex * s.ldm);
+                     : (c->tc ? (c->tc3 ? 2 : 1) * (int64_t)s.ey * mp8 * mp8 : (int64_t)s.ey * s.ex * s.ldm);
       s.soff = soff; soff += (int64_t)s.ex * s.ey;
       s.woff = woff; woff += 2 * (int64_t)s.ex * s.ex;
       s.aoff = aoff; aoff += 2 * s.ex + 2 * s.ey + 2;
@@ -201,6 +204,10 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   if (c->max_m > kMaxBoxWidth) {
     free_ctx(c);
     return invalid("hd_setup_medium: a box is wider than 256 cells (use more boxes along x)");
+  }
+  if (c->tc3 && c->max_m > kMaxBoxWidthX3) {
+    free_ctx(c);
+    return invalid("hd_setup_medium: HD_TF32X3 takes boxes up to 176 cells wide (use more boxes along x)");
   }
   c->factor_elems = foff; c->staging_elems = soff; c->work_elems = woff;
   const int64_t n = (int64_t)c->NX * c->NY;

@@ -90,7 +90,8 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
          double h2, S *__restrict__ factor, C<R> *__restrict__ work, int32_t *status, const int32_t *only) {
   if (only && only[blockIdx.x] == 0) return;   // refactor only the boxes the tensor-core kernel marked
   using T = C<R>;
-  constexpr bool SYM = LAY == LAY_SYM, TCL = LAY == LAY_TC;
+  constexpr bool SYM = LAY == LAY_SYM, TCL = LAY == LAY_TC || LAY == LAY_TC3;
+  constexpr int NPL = LAY == LAY_TC3 ? 4 : 2;   // planes per chunk of the tensor-core layouts
   // S_{j+1} is kept in W2 when the stored copy is narrower than the arithmetic
   constexpr bool KEEP2 = sizeof(S) != sizeof(T) || TCL;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -116,7 +117,8 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
   const int64_t mt16 = (m + 15) / 16;
   const int mp8 = (m + 7) & ~7;
   const int64_t mm = (int64_t)m * m;
-  const int64_t slot_elems = SYM ? mt16 * (mt16 + 1) / 2 * 256 : (TCL ? (int64_t)mp8 * mp8 : (int64_t)m * ldm);
+  const int64_t slot_elems =
+      SYM ? mt16 * (mt16 + 1) / 2 * 256 : (TCL ? (int64_t)(NPL / 2) * mp8 * mp8 : (int64_t)m * ldm);
   bool bad = false;
 
   // ---- S_0 = D_0
@@ -362,20 +364,23 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
         if (TCL) {
           // chunks 2J, 2J+1 (8 columns each) of the block, each the real then the imaginary
           // plane [mp8/8 row groups][2 core matrices along K][8 rows][4 columns], TF32
+          // (LAY_TC3: then the real and imaginary remainders, also TF32)
           float *F = reinterpret_cast<float *>(slot);
           const int per = 8 * mp8;   // floats of one plane of one chunk
-          for (int idx = tid; idx < 4 * per; idx += FT) {
+          for (int idx = tid; idx < 2 * NPL * per; idx += FT) {
             const int cp = idx / per, w = idx - cp * per;
-            const int ch = 2 * J + (cp >> 1), P = cp & 1;
+            const int ch = 2 * J + cp / NPL, P = cp % NPL;
             if (ch >= mp8 / 8) continue;
             const int g = w >> 6, kk = (w >> 5) & 1, rr = (w >> 2) & 7, c4 = w & 3;
             const int r = 8 * g + rr, c = 8 * ch + 4 * kk + c4;
             float v = 0.f;
             if (r < m && c < m) {
               const T q = Q[(c - c0) * m + r];
-              v = tf32_round((float)(P ? q.y : q.x));
+              const float x = (float)((P & 1) ? q.y : q.x);
+              v = tf32_round(x);
+              if (P >= 2) v = tf32_round(x - v);
             }
-            F[(int64_t)ch * 2 * per + (int64_t)P * per + w] = v;
+            F[(int64_t)ch * NPL * per + (int64_t)P * per + w] = v;
           }
         }
       }
@@ -404,7 +409,8 @@ static cudaError_t launch_factor_r(hd_ctx *ctx, void *factor, void *work, const 
 }
 
 static cudaError_t launch_factor_simt(hd_ctx *ctx, void *factor, void *work, const int32_t *only, cudaStream_t st) {
-  return ctx->tc                  ? launch_factor_rs<float, float2, LAY_TC>(ctx, factor, work, only, st)
+  return ctx->tc3                 ? launch_factor_rs<float, float2, LAY_TC3>(ctx, factor, work, only, st)
+         : ctx->tc               ? launch_factor_rs<float, float2, LAY_TC>(ctx, factor, work, only, st)
          : ctx->prec == HD_C64   ? launch_factor_r<float, float2>(ctx, factor, work, only, st)
          : ctx->prec == HD_C64_H ? launch_factor_r<float, __half2>(ctx, factor, work, only, st)
          : ctx->prec == HD_C64_B ? launch_factor_r<float, __nv_bfloat162>(ctx, factor, work, only, st)

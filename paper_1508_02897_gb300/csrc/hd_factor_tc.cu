@@ -124,14 +124,21 @@ template <typename S, int LAY>
 __device__ __forceinline__ void emit(S *slot, int r, int c, float2 v, int m, int ldm, int mp8) {
   if (LAY == LAY_FULL) {
     if (r < m && c < m) slot[(int64_t)c * ldm + r] = store_c<S>(v);
-  } else {   // LAY_TC: chunk c/8, real then imaginary plane [mp8/8][2][8][4], TF32
+  } else {   // LAY_TC: chunk c/8, real then imaginary plane [mp8/8][2][8][4], TF32;
+             // LAY_TC3: then the real and imaginary remainders, TF32
     if (r >= mp8 || c >= mp8) return;
     if (r >= m || c >= m) v = make_float2(0.f, 0.f);
     float *F = reinterpret_cast<float *>(slot);
     const int per = 8 * mp8;
-    const int64_t o = (int64_t)(c >> 3) * 2 * per + (r >> 3) * 64 + ((c >> 2) & 1) * 32 + (r & 7) * 4 + (c & 3);
-    F[o] = tf32_round(v.x);
-    F[o + per] = tf32_round(v.y);
+    constexpr int NPL = LAY == LAY_TC3 ? 4 : 2;
+    const int64_t o = (int64_t)(c >> 3) * NPL * per + (r >> 3) * 64 + ((c >> 2) & 1) * 32 + (r & 7) * 4 + (c & 3);
+    const float hr = tf32_round(v.x), hi = tf32_round(v.y);
+    F[o] = hr;
+    F[o + per] = hi;
+    if (LAY == LAY_TC3) {
+      F[o + 2 * per] = tf32_round(v.x - hr);
+      F[o + 3 * per] = tf32_round(v.y - hi);
+    }
   }
 }
 
@@ -188,7 +195,9 @@ k_factor_tc(const SubDev *__restrict__ subs, int nsub, const double2 *__restrict
     const double2 *ia2f = a2c + rows;
     S *Fs = factor + s.foff;
     const int64_t slot_elems = LAY == LAY_SYM ? (int64_t)mt * (mt + 1) / 2 * 256
-                                              : (LAY == LAY_TC ? (int64_t)mp8 * mp8 : (int64_t)m * s.ldm);
+                                              : (LAY == LAY_TC    ? (int64_t)mp8 * mp8
+                                                 : LAY == LAY_TC3 ? 2 * (int64_t)mp8 * mp8
+                                                                  : (int64_t)m * s.ldm);
     const uint32_t idesc_top = tc::idesc_bf16(128, NP);
     const uint32_t idesc_bot = tc::idesc_bf16(128, NB > 0 ? NB : 16);
 
@@ -628,6 +637,7 @@ bool factor_tc_supported(const hd_ctx *ctx) { return ctx->prec != HD_C128 && ctx
 
 cudaError_t launch_factor_tc(hd_ctx *ctx, void *factor, cudaStream_t st) {
   const float tau2 = (float)(ctx->fpivot * ctx->fpivot);
+  if (ctx->tc3) return launch_tc<float2, LAY_TC3>(ctx, factor, tau2, st);
   if (ctx->tc) return launch_tc<float2, LAY_TC>(ctx, factor, tau2, st);
   if (ctx->prec == HD_C64)
     return ctx->sym ? launch_tc<float2, LAY_SYM>(ctx, factor, tau2, st) : launch_tc<float2, LAY_FULL>(ctx, factor, tau2, st);

@@ -177,7 +177,9 @@ __device__ __forceinline__ T d_band(int r, int c, int j, const double2 *a1c, con
 
 // Storage layouts of the S_j^{-1}: full column-major blocks, upper 16 x 16 tiles,
 // or TF32 real/imaginary planes in the tensor-core operand layout (HD_TCORE).
-enum { LAY_FULL = 0, LAY_SYM = 1, LAY_TC = 2 };
+// LAY_TC3: the same layout with four planes per chunk (real hi, imaginary hi, real lo,
+// imaginary lo), hi = TF32 rounding and lo = TF32 rounding of the remainder (HD_TF32X3).
+enum { LAY_FULL = 0, LAY_SYM = 1, LAY_TC = 2, LAY_TC3 = 3 };
 
 __device__ __forceinline__ float tf32_round(float x) {
   uint32_t r;
@@ -235,6 +237,7 @@ struct hd_ctx {
   int prec;
   bool sym = false;   // S_j^{-1} stored as upper 16 x 16 tiles (HD_SYMMETRIC)
   bool tc = false;    // S_j^{-1} stored in the tensor-core operand layout (HD_TCORE)
+  bool tc3 = false;   // ... as TF32 hi/lo pairs, FP32-grade products (HD_TF32X3)
   bool smooth = false;   // local solutions weighted by the smoothing function beta (HD_SMOOTH)
   // decomposition
   int nbx, nby, overlap, own_global_pml;
@@ -311,6 +314,10 @@ cudaError_t launch_residual_strided(hd_ctx *ctx, const double2 *b, int64_t bs, c
                                     double2 *r, int64_t rs, int nrhs, cudaStream_t st);
 // Restrict + forward/back substitution on the tensor cores (HD_TCORE storage), staging out.
 cudaError_t launch_subst_tc(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec_stride, void *staging,
+                            int64_t stg_stride, cudaStream_t st);
+// The FP32-grade tensor-core substitution (hd_subst_x3.cu, storage HD_TCORE | HD_TF32X3).
+constexpr int kMaxBoxWidthX3 = 176;
+cudaError_t launch_subst_x3(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec_stride, void *staging,
                             int64_t stg_stride, cudaStream_t st);
 size_t krylov_bytes(int64_t n, int restart, int nrhs);
 int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st, int *ct_out,

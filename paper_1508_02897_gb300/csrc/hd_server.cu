@@ -95,7 +95,8 @@ static size_t request_bytes(const Request &q, int batch) {
       const size_t mt = (b + 15) / 16;
       const size_t mp8 = (b + 7) & ~7;
       factor += sym ? (size_t)a * mt * (mt + 1) / 2 * 256
-                    : ((q.precision & HD_TCORE) ? (size_t)a * mp8 * mp8 : (size_t)a * b * ((b + 3) & ~3));
+                    : ((q.precision & HD_TCORE) ? ((q.precision & HD_TF32X3) ? 2 : 1) * (size_t)a * mp8 * mp8
+                                                : (size_t)a * b * ((b + 3) & ~3));
       staging += (size_t)a * b;
       work += 2 * (size_t)b * b;
     }
@@ -235,7 +236,8 @@ int hd_submit(hd_server *s, const hd_grid *grid, const hd_decomp *dec, const dou
       opts->restart > HD_MAX_RESTART ||
       ((precision & 0xff) != HD_C64 && (precision & 0xff) != HD_C128 && (precision & 0xff) != HD_C64_H &&
        (precision & 0xff) != HD_C64_B) ||
-      (precision & ~(0xff | HD_SYMMETRIC | HD_TCORE | HD_SMOOTH)) ||
+      (precision & ~(0xff | HD_SYMMETRIC | HD_TCORE | HD_TF32X3 | HD_SMOOTH)) ||
+      ((precision & HD_TF32X3) && !(precision & HD_TCORE)) ||
       ((precision & HD_TCORE) && ((precision & 0xff) != HD_C64 || (precision & HD_SYMMETRIC)))) {
     set_error("hd_submit: bad argument");
     return HD_ERR_INVALID;

@@ -688,7 +688,8 @@ static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, dou
                                   void *staging, cudaStream_t st) {
   if (ctx->tc || ctx->sym) {
     tic(ctx, T_SUBST, st);
-    cudaError_t e = ctx->tc ? launch_subst_tc(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
+    cudaError_t e = ctx->tc3  ? launch_subst_x3(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
+                    : ctx->tc ? launch_subst_tc(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
                     : (ctx->max_m <= 192 && ctx->tune_ct != 256)
                         ? launch_subst_sym_nr<R, S, 6>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st)
                         : launch_subst_sym_nr<R, S, 8>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st);

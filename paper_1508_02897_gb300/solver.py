@@ -16,14 +16,17 @@ def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> int:
     return int(s.cuda_stream)
 
 
-def _storage_flag(prec: int, symmetric: bool, tcore: bool, smoothing: bool = False) -> int:
-    """Storage of the S_j^{-1} (tensor-core operand layout, c64 only; upper tiles; or
-    full) and the optional smoothing function of the sum of local solutions."""
+def _storage_flag(prec: int, symmetric: bool, tcore, smoothing: bool = False) -> int:
+    """Storage of the S_j^{-1} (tensor-core operand layout, c64 only: ``tcore`` True or
+    "tf32" for TF32 planes, "x3" for TF32 hi/lo pairs with FP32-grade products; upper
+    tiles; or full) and the optional smoothing function of the sum of local solutions."""
     sm = B.HD_SMOOTH if smoothing else 0
     if tcore:
         if prec != B.HD_C64:
             raise ValueError("tensor-core storage needs precision c64")
-        return B.HD_TCORE | sm
+        if tcore not in (True, "tf32", "x3"):
+            raise ValueError("tcore: False, True / 'tf32' or 'x3'")
+        return B.HD_TCORE | (B.HD_TF32X3 if tcore == "x3" else 0) | sm
     return (B.HD_SYMMETRIC if symmetric else 0) | sm
 
 
@@ -38,7 +41,7 @@ class HelmholtzDDM:
                  precision: str = "c64", cut_x: Optional[Sequence[int]] = None, cut_y: Optional[Sequence[int]] = None,
                  own_global_pml: bool = True, sigma0_over_omega: float = 20.0, pml_power: int = 2,
                  device: str = "cuda", stream: Optional[torch.cuda.Stream] = None, factor: bool = True,
-                 symmetric: bool = True, tcore: bool = False, smoothing: bool = False,
+                 symmetric: bool = True, tcore=False, smoothing: bool = False,
                  factor_path: str = "auto", pivot_ratio: float = 0.5):
         if not torch.cuda.is_available():
             raise RuntimeError("HelmholtzDDM needs a CUDA device: there is no CPU path")

@@ -33,15 +33,16 @@ def test_invalid_arguments_are_rejected_without_gpu():
 
 def test_storage_flags_and_new_entry_points_validate_without_gpu():
     """Host-side checks run before any CUDA call: the tensor-core storage flag is
-    refused with FP64 factors or together with symmetric storage, an unknown flag
-    bit is refused, and the multi-step DDM and FGMRES entry points refuse NULL
+    refused with FP64 factors or together with symmetric storage, the split-TF32 flag
+    without the tensor-core storage, an unknown flag bit is refused, and the multi-step DDM and FGMRES entry points refuse NULL
     contexts, zero steps and bad options."""
     from paper_1508_02897_gb300 import _binding as B
     L = B.lib()
     g = B.hd_grid(64, 64, 8, 1.0 / 64, 40.0, 20.0, 2)
     d = B.hd_decomp(2, 2, 4, None, None, 1)
     fake_c = ctypes.c_void_p(16)   # never dereferenced: validation fails first
-    for prec in (B.HD_C128 | B.HD_TCORE, B.HD_C64 | B.HD_TCORE | B.HD_SYMMETRIC, B.HD_C64 | 0x800, 7):
+    for prec in (B.HD_C128 | B.HD_TCORE, B.HD_C64 | B.HD_TCORE | B.HD_SYMMETRIC, B.HD_C64 | B.HD_TF32X3,
+                 B.HD_C64 | 0x1000, 7):
         ctx = ctypes.c_void_p()
         rc = L.hd_setup_medium(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(d), fake_c, prec, None)
         assert rc == B.HD_ERR_INVALID and not ctx.value, prec

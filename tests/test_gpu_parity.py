@@ -9,7 +9,8 @@ stores the local factors in complex FP32: preconditioner 2e-4 relative L2
 solution 1e-5 against the FP64 oracle at relative residual 1e-8.  Reduced-precision
 storage of the factors scales that bound by its unit roundoff over FP32's: TF32 and
 FP16 storage (2^-11) 3e-2, BF16 storage (2^-8, eight times coarser) 1.2e-1; the FP64
-outer loop still reaches its tolerance.
+outer loop still reaches its tolerance.  The split-TF32 tensor-core storage (c64x: hi/lo
+TF32 pairs, products to about FP32's unit roundoff) keeps the FP32 bound, 2e-4.
 """
 import numpy as np
 import pytest
@@ -52,13 +53,20 @@ def oracle(name, own=True):
 
 
 def gpu(name, precision, own=True):
-    """precision: c128 / c64 / c64h, with a trailing "s" for symmetric tile storage or
-    "t" for the tensor-core storage (c64t: TF32 factors, tcgen05 substitution)."""
+    """precision: c128 / c64 / c64h, with a trailing "s" for symmetric tile storage,
+    "t" for the tensor-core storage (c64t: TF32 factors, tcgen05 substitution) or "x"
+    for the split-TF32 tensor-core storage (c64x: FP32-grade products)."""
     case, c, g, _, _ = oracle(name, own)
-    sym, tc = precision.endswith("s"), precision.endswith("t")
+    sym = precision.endswith("s")
+    tc = "x3" if precision.endswith("x") else precision.endswith("t")
     return HelmholtzDDM(case["N"], case["npml"], g.omega, c, case["nb"], case["nb"], case["overlap"],
-                        precision=precision.rstrip("st"), cut_x=cuts(case), cut_y=cuts(case), own_global_pml=own,
+                        precision=precision.rstrip("stx"), cut_x=cuts(case), cut_y=cuts(case), own_global_pml=own,
                         symmetric=sym, tcore=tc)
+
+
+def _x3_fits(name):
+    """The split-TF32 storage takes boxes up to 176 cells wide (the "wide" case has 178)."""
+    return name != "wide"
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -78,9 +86,14 @@ def test_matvec_and_rhs(name):
 @pytest.mark.parametrize("name", list(CASES))
 @pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64", 2e-4), ("c64h", 3e-2), ("c128s", 1e-10),
                                            ("c64s", 2e-4), ("c64hs", 3e-2), ("c64t", 3e-2), ("c64b", 1.2e-1),
-                                           ("c64bs", 1.2e-1)])
+                                           ("c64bs", 1.2e-1), ("c64x", 2e-4)])
 def test_precond_parity(name, precision, tol):
     _, _, g, _, P = oracle(name)
+    if precision == "c64x" and not _x3_fits(name):
+        from paper_1508_02897_gb300._binding import HDError
+        with pytest.raises(HDError):
+            gpu(name, precision)
+        return
     s = gpu(name, precision)
     r = W.random_complex((g.n, g.n), seed=3)
     z = s.apply_precond(torch.from_numpy(r)).cpu().numpy()
@@ -134,12 +147,14 @@ def test_gmres_converged_c128(name, arnoldi, reorth):
 
 
 @pytest.mark.parametrize("name", list(CASES))
-@pytest.mark.parametrize("precision", ["c64", "c64h", "c64s", "c64t", "c64bs"])
+@pytest.mark.parametrize("precision", ["c64", "c64h", "c64s", "c64t", "c64bs", "c64x"])
 def test_gmres_mixed_precision(name, precision):
-    """FP32 local factors (stored in FP32, FP16 or TF32), FP64 outer loop: the FP64
-    relative residual reaches the tolerance and the solution matches the FP64
+    """FP32 local factors (stored in FP32, FP16, TF32 or split TF32), FP64 outer loop: the
+    FP64 relative residual reaches the tolerance and the solution matches the FP64
     oracle to 1e-5."""
     case, c, g, A, P = oracle(name)
+    if precision == "c64x" and not _x3_fits(name):
+        pytest.skip("boxes wider than the split-TF32 storage takes")
     s = gpu(name, precision)
     f = W.gaussian_source(case["N"], case["npml"], 0.5, 0.5, 2.0 / case["N"])
     b = rhs_from_source(g, f)
@@ -174,12 +189,13 @@ def _sources(case, k, seed):
 
 
 @pytest.mark.parametrize("precision,nrhs", [("c128", 3), ("c64", 9), ("c64s", 5), ("c64t", 5), ("c64t", 19),
-                                             ("c64t", 37)])
+                                             ("c64t", 37), ("c64x", 5), ("c64x", 70)])
 def test_precond_batched_equals_single(precision, nrhs):
     """Each right-hand side of a batched application (groups of up to 8 per CTA, 16
     on the tensor cores; 37 sources there give two full groups and a ragged one of 5,
-    launched side by side per box) gives bitwise the same vector as its own
-    application."""
+    launched side by side per box; 32 per CTA with the split-TF32 storage, 70 sources
+    giving two full groups and a ragged one of 6) gives bitwise the same vector as its
+    own application."""
     _, _, g, _, P = oracle("ragged")
     s = gpu("ragged", precision)
     r = W.random_complex((nrhs, g.n, g.n), seed=12)
@@ -192,10 +208,13 @@ def test_precond_batched_equals_single(precision, nrhs):
         zk = s.apply_precond(torch.from_numpy(r[k])).cpu().numpy()
         assert np.array_equal(z[k], zk)
     tol = 1e-10 if precision.startswith("c128") else (3e-2 if precision.endswith("t") else 2e-4)
+    if precision == "c64x":   # every source in the groups of 32 against the oracle
+        for k in (0, 31, 32, nrhs - 1) if nrhs > 32 else range(nrhs):
+            assert rel(z[k], P.apply(r[k])) < tol
     assert rel(z[nrhs - 1], P.apply(r[nrhs - 1])) < tol
 
 
-@pytest.mark.parametrize("precision", ["c128", "c64", "c64t"])
+@pytest.mark.parametrize("precision", ["c128", "c64", "c64t", "c64x"])
 def test_gmres_batched_alone_vs_mix(precision):
     """Lockstep solve of several sources sharing one factorisation: every
     solution is bitwise the one its source gets alone, and matches the oracle."""
@@ -243,7 +262,7 @@ def test_gmres_graph_capture_matches_launches(precision, reorth):
 
 # ---------------------------------------------------------------- multi-step DDM
 @pytest.mark.parametrize("name", ["ragged", "layers4"])
-@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64s", 5e-4), ("c64t", 5e-2)])
+@pytest.mark.parametrize("precision,tol", [("c128", 1e-10), ("c64s", 5e-4), ("c64t", 5e-2), ("c64x", 5e-4)])
 def test_multistep_ddm_parity(name, precision, tol):
     """hd_apply_ddm (residual correction on the GPU) against the oracle's literal
     Eq. (ddms) (neighbour residuals per box) for 1, 2 and 3 steps, two sources."""

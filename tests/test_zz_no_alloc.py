@@ -41,7 +41,7 @@ def _noalloc_fn():
 # sources than the 64 MiB array holds at once (0.9 MB of staging each), so the entry point
 # runs them in two groups
 CASES = [("c128", False, False, 2), ("c64", False, False, 2), ("c64", True, False, 2), ("c64h", True, False, 2),
-         ("c64h", False, False, 2), ("c64", False, True, 9), ("c64", True, False, 80)]
+         ("c64h", False, False, 2), ("c64", False, True, 9), ("c64", False, "x3", 33), ("c64", True, False, 80)]
 
 
 @pytest.mark.parametrize("precision,sym,tcore,nrhs", CASES)
