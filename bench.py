@@ -73,14 +73,17 @@ def parse():
                    help="weight each local solution by the smoothing function beta (Remark after Eq. (pc))")
     p.add_argument("--precond-steps", type=int, default=1,
                    help="steps of the overlapping DDM used as the preconditioner (Eq. (ddms); 1: Eq. (pc))")
-    p.add_argument("--storage", default="auto", choices=("auto", "sym", "full", "tc"),
-                   help="S_j^{-1} storage: upper 16x16 tiles (sym), full blocks, or TF32 planes for the "
-                        "tensor-core substitution (tc); auto: tc for lockstep groups of 8 or more sources, else sym")
+    p.add_argument("--storage", default="auto", choices=("auto", "sym", "full", "tc", "x3"),
+                   help="S_j^{-1} storage: upper 16x16 tiles (sym), full blocks, TF32 planes for the tensor-core "
+                        "substitution (tc), or TF32 hi/lo pairs for its FP32-grade form (x3); auto: x3 (tc where a "
+                        "box is wider than 176) for lockstep groups of 8 or more sources, else sym")
     p.add_argument("--symmetric", dest="storage", action="store_const", const="sym", help="same as --storage sym")
     p.add_argument("--full-blocks", dest="storage", action="store_const", const="full", help="same as --storage full")
     p.add_argument("--overlap", type=int, default=None, help="extra overlap lo in cells (default 8)")
     p.add_argument("--npml", type=int, default=None, help="PML cells per side (default 16)")
     p.add_argument("--nrhs", type=int, default=None, help="sources per solve (batching config: 64)")
+    p.add_argument("--N", type=int, default=None, help="interior cells per side (profiling: a smaller grid of the config)")
+    p.add_argument("--nb", type=int, default=None, help="boxes per side (with --N)")
     p.add_argument("--group", type=int, default=64, help="sources solved together in lockstep (default: all of the batching workload)")
     p.add_argument("--single-sample", type=int, default=2, help="batching: sources also solved one at a time")
     p.add_argument("--no-legs", dest="legs", action="store_false",
@@ -187,7 +190,8 @@ class Clocks:
 # ----------------------------------------------------------------------------- workload
 def workload(args, rank: int):
     nrhs = args.nrhs or (64 if args.config == "batching" else 1)
-    extra = {k: v for k, v in (("overlap", getattr(args, "overlap", None)), ("npml", getattr(args, "npml", None)))
+    extra = {k: v for k, v in (("overlap", getattr(args, "overlap", None)), ("npml", getattr(args, "npml", None)),
+                               ("N", getattr(args, "N", None)), ("nb", getattr(args, "nb", None)))
              if v is not None}
     wl = W.make_workload(args.config, restart=args.restart, rtol=args.rtol, nrhs=nrhs, **extra)
     if rank > 0:  # every rank solves its own problem: same medium, its own source position
@@ -209,11 +213,11 @@ def _rhs_per_cta(k):
 
 
 def block_entries(m: int, storage) -> int:
-    """Stored entries of one S_j^{-1}: m^2 (full), the upper 16x16 tiles (sym), or
-    (m rounded up to 8)^2 (tc)."""
-    if storage == "tc":
+    """Stored 8-byte entries of one S_j^{-1}: m^2 (full), the upper 16x16 tiles (sym),
+    (m rounded up to 8)^2 (tc: TF32 real and imaginary), twice that (x3: hi/lo pairs)."""
+    if storage in ("tc", "x3"):
         mp8 = -(-m // 8) * 8
-        return mp8 * mp8
+        return mp8 * mp8 * (2 if storage == "x3" else 1)
     if storage in (False, "full"):
         return m * m
     mt = -(-m // 16)
@@ -226,7 +230,7 @@ def subst_bytes(wl, cs: int, nrhs: int = 1, fs: int = None, sym=False) -> int:
     backward (the last row once) per group of right-hand sides sharing a CTA, the
     owned residual read once (FP64 complex), the staging vector written forward,
     read and rewritten backward."""
-    per_cta = 16 if sym == "tc" else _rhs_per_cta(nrhs)
+    per_cta = {"tc": 16, "x3": 32}.get(sym) or _rhs_per_cta(nrhs)
     groups = -(-nrhs // per_cta)
     tot = 16 * wl.n * wl.n * nrhs
     for iy in range(wl.nby):
@@ -263,7 +267,7 @@ def run_ours(args, world, rank, local):
 
     group = max(1, min(args.group, wl.nrhs))
     if args.storage == "auto":   # tensor cores pay once a lockstep group is wide enough
-        args.storage = "tc" if group >= 8 and args.precision == "c64" else "sym"
+        args.storage = _tc_storage(wl) if group >= 8 and args.precision == "c64" else "sym"
 
     def one_solve(precision, profile, f=None, grp=None, storage=None, arnoldi=None, graphs=False):
         f = f_d if f is None else f
@@ -272,7 +276,7 @@ def run_ours(args, world, rank, local):
         arnoldi = arnoldi or (args.arnoldi if precision == args.precision else "fp64")
         s = HelmholtzDDM(wl.N, wl.npml, wl.omega, c_d, wl.nbx, wl.nby, wl.overlap, precision=precision,
                          cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev),
-                         symmetric=storage == "sym", tcore=storage == "tc" and precision == "c64",
+                         symmetric=storage == "sym", tcore=_tcore_arg(storage) if precision == "c64" else False,
                          smoothing=args.smoothing)
         s.set_profiling(profile)
         s.factor()
@@ -369,7 +373,9 @@ def run_ours(args, world, rank, local):
                        _factor_gb(wl, fs, sym), 2 * (wl.restart + 1) * n_unk * 16 / 1e9),
                    "precond_steps": args.precond_steps, "smoothing": bool(args.smoothing),
                    "factor_storage": {"sym": "upper 16x16 tiles (symmetric)", "full": "full blocks",
-                                      "tc": "TF32 real/imag planes, tensor-core operand layout"}[sym],
+                                      "tc": "TF32 real/imag planes, tensor-core operand layout",
+                                      "x3": "TF32 hi/lo pairs of real/imag planes, tensor-core operand layout "
+                                            "(FP32-grade products)"}[sym],
                    "parallelism": f"replicas x{world} (one independent solve per GPU)"},
         "unknown_iters_per_s": unk_iters,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
@@ -383,7 +389,7 @@ def run_ours(args, world, rank, local):
                              "mode": args.reorth},
         "breakdown_ms_per_step": {c: cls_ms[c] / args.steps for c in classes},
         "dominant_kernel_class": dominant,
-        "roofline": {"kernel": {"sym": "k_subst_sym", "tc": "k_subst_tc", "full": "k_subst"}[sym]
+        "roofline": {"kernel": {"sym": "k_subst_sym", "tc": "k_subst_tc", "x3": "k_subst_x3", "full": "k_subst"}[sym]
                                + " (restrict + forward/back substitution)",
                      "bound": "hbm",
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -474,7 +480,7 @@ def run_ours(args, world, rank, local):
             t = srv.submit(c_h.numpy(), f_h.numpy(), wl.N, wl.npml, wl.omega, wl.nbx, wl.nby, wl.overlap,
                            wl.restart, wl.rtol, args.max_iters, precision=args.precision, cut_x=wl.cut_x,
                            cut_y=wl.cut_y, arnoldi=args.arnoldi, reorth=args.reorth,
-                           symmetric=args.storage == "sym", tcore=args.storage == "tc", out=x_h.numpy())
+                           symmetric=args.storage == "sym", tcore=_tcore_arg(args.storage), out=x_h.numpy())
             _, st_e, _ = srv.poll(t)
             est.extend(st_e)
         te = max_over_ranks(time.perf_counter() - t0, world)
@@ -500,8 +506,8 @@ def run_ours(args, world, rank, local):
 def batching_leg(args, dev, local, warmup=1, steps=2):
     """The batching configuration: 1984^2 random medium, 16 x 16 boxes (edge boxes 96^2
     owned), 64 Gaussian sources sharing one factorisation, solved as one lockstep group with
-    the tensor-core substitution and every Arnoldi step replayed from a CUDA graph.  One step
-    = factorisation + the 64-source solve; solves/s counts sources."""
+    the FP32-grade (split-TF32) tensor-core substitution and every Arnoldi step replayed from
+    a CUDA graph.  One step = factorisation + the 64-source solve; solves/s counts sources."""
     import copy
     import torch
     from paper_1508_02897_gb300.solver import HelmholtzDDM
@@ -514,7 +520,8 @@ def batching_leg(args, dev, local, warmup=1, steps=2):
 
     def step(profile):
         s = HelmholtzDDM(wl.N, wl.npml, wl.omega, c_d, wl.nbx, wl.nby, wl.overlap, precision="c64",
-                         cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev), symmetric=False, tcore=True)
+                         cut_x=wl.cut_x, cut_y=wl.cut_y, factor=False, device=str(dev), symmetric=False,
+                         tcore=_tcore_arg(_tc_storage(wl)))
         s.set_profiling(profile)
         s.factor()
         b = s.rhs(f_d)
@@ -547,7 +554,8 @@ def batching_leg(args, dev, local, warmup=1, steps=2):
             "steps": steps, "warmup": warmup, "ms_per_step": tot * 1e3 / steps,
             "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
             "sources_per_step": wl.nrhs, "lockstep_group": wl.nrhs, "cuda_graphs": True,
-            "factor_storage": "TF32 real/imag planes, tensor-core substitution",
+            "factor_storage": {"x3": "TF32 hi/lo pairs (FP32-grade products), tensor-core substitution",
+                               "tc": "TF32 real/imag planes, tensor-core substitution"}[_tc_storage(wl)],
             "iters": {"mean": float(np.mean(its)), "min": int(min(its)), "max": int(max(its))},
             "relres_true_max": float(max(x["relres_true"] for x in stats)),
             "converged": all(x["converged"] == 1 for x in stats),
@@ -575,12 +583,25 @@ def serving_legs(args, world, rank, local):
     return legs
 
 
+def _tc_storage(wl):
+    """Tensor-core storage for a workload: the FP32-grade split-TF32 pairs where every box
+    fits them (at most 176 cells wide), else TF32 planes."""
+    widest = max(_extent(wl.cut_x, ix, wl) for ix in range(wl.nbx))
+    return "x3" if widest <= 176 else "tc"
+
+
+def _tcore_arg(storage):
+    return {"tc": True, "x3": "x3"}.get(storage, False)
+
+
 def _dtype_label(args):
     """Arithmetic of the path: local factors and substitutions, Gram-Schmidt, outer loop."""
     fac = {"c64": "c64 factors", "c64h": "c64 factors stored c32 (FP16 pairs)",
            "c64b": "c64 factors stored c32 (BF16 pairs)", "c128": "c128 factors"}[args.precision]
     if args.storage == "tc":
         fac += " (TF32 storage, tensor-core substitution)"
+    elif args.storage == "x3":
+        fac += " (split-TF32 storage, FP32-grade tensor-core substitution)"
     ds = args.arnoldi == "ds" or (args.arnoldi == "auto" and args.precision != "c128")
     gs = "ds48 Gram-Schmidt (float pairs, ~48-bit)" if ds else "f64 Gram-Schmidt"
     return f"{fac} + {gs} + f64 outer (Hessenberg, Givens, true residual)"
@@ -607,7 +628,7 @@ def _factor_gb(wl, cs, sym=False):
 def _profile_traffic(wl, args):
     """DRAM bytes per k_subst launch from the committed ncu summary, scaled to
     this workload, when it matches the current kernel (else None)."""
-    if args.storage == "tc":
+    if args.storage in ("tc", "x3"):
         return None
     name = "k_subst_sym_traffic.json" if args.storage == "sym" else "k_subst_traffic.json"
     path = os.path.join(ROOT, "profiles", name)
@@ -666,7 +687,8 @@ def run_serving(args, world, rank, local):
         if t_arr > now:
             time.sleep(t_arr - now)
         # storage per request: tensor cores for 8 or more sources (auto), else symmetric tiles
-        tc = args.storage == "tc" or (args.storage == "auto" and wl.nrhs >= 8 and args.precision == "c64")
+        tc = (_tcore_arg(args.storage) or
+              (args.storage == "auto" and wl.nrhs >= 8 and args.precision == "c64" and _tcore_arg(_tc_storage(wl))))
         tickets.append((srv.submit(wl.c, wl.f, wl.N, wl.npml, wl.omega, wl.nbx, wl.nby, wl.overlap, wl.restart,
                                    wl.rtol, args.max_iters, precision=args.precision,
                                    symmetric=not tc and args.storage in ("sym", "auto"), tcore=tc,

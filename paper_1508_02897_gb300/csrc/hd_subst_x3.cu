@@ -25,10 +25,15 @@
 // writes those rows of the output and the same 32 columns of the next step's V into
 // A1/A2 (the next step's K range), and arrives on that column group's mbarrier; the MMAs
 // of step t + 1 start on a column group as soon as it is complete, into the other
-// accumulator, so the tensor cores work while the epilogue runs.
+// accumulator, so the tensor cores work while the epilogue runs.  Each epilogue thread
+// issues the global loads of the operands of its whole step that do not depend on the
+// product (the staged w_j of a backward step, the next grid row's residual of a forward
+// step) before it waits for the accumulator.
 //
 // Warp roles: warps 0-3 epilogue (thread = tensor-memory lane), warp 4 producer (factor
-// chunks through an mbarrier ring with cp.async.bulk, in use order across steps), warp 5
+// chunks through an mbarrier ring with cp.async.bulk, in use order across steps, after
+// asking L2 for them a few chunks ahead: the ring holds two to four chunks beside the A
+// operands, too few to cover HBM's latency on its own), warp 5
 // tensor-memory owner and MMA issuer (one thread).  Every wait is bounded (flag
 // ST_TIMEOUT and unwind); tensor memory is released only after a final commit confirms
 // that no MMA is in flight and the epilogue has finished reading it.
@@ -47,6 +52,7 @@ constexpr uint32_t X3_HALF = 256;             // column offset of the odd-step a
 constexpr uint32_t kX3Lbo = 128;              // A1/A2: bytes between core matrices along K
 constexpr int X3_GROUPS = (kMaxBoxWidthX3 + 31) / 32;   // 32-column groups of the widest box
 constexpr size_t kX3Tail = 256;               // the last plane's N padding (m rounded to 16) reads past the ring
+constexpr int kX3Prefetch = 8;                // chunks the producer asks L2 for ahead of its copies
 
 __device__ __forceinline__ void bar_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::su32(bar)) : "memory");
@@ -59,6 +65,9 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t b
                    tc::su32(dst)),
                "l"(src), "r"(bytes), "r"(tc::su32(bar))
                : "memory");
+}
+__device__ __forceinline__ void prefetch_l2(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
@@ -193,19 +202,24 @@ k_subst_x3(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, co
   const uint32_t chunk_bytes = (uint32_t)(128 * mp8);
 
   if (warp == 4) {
-    // ---------------- producer: chunks of every block in use order
+    // ---------------- producer: chunks of every block in use order, each asked of L2
+    // kX3Prefetch chunks before its copy
     if (lane == 0) {
+      auto chunk_src = [&](int64_t it) {
+        const int st = (int)(it / nck), c = (int)(it - (int64_t)st * nck);
+        const int j = st < rows ? st : 2 * rows - 2 - st;
+        return Fs + j * slot_floats + (int64_t)c * 32 * mp8;
+      };
+      for (int64_t it = 0; it < min(total, (int64_t)kX3Prefetch); ++it) prefetch_l2(chunk_src(it), chunk_bytes);
       int64_t issued = 0;
       bool ok = true;
       for (int64_t it = 0; it < total && ok; ++it) {
-        const int st = (int)(it / nck), c = (int)(it - (int64_t)st * nck);
-        const int j = st < rows ? st : 2 * rows - 2 - st;
+        if (it + kX3Prefetch < total) prefetch_l2(chunk_src(it + kX3Prefetch), chunk_bytes);
         const int slot = (int)(it % NS);
         const uint32_t ph = (uint32_t)((it / NS) & 1);
-        if (!tc::bar_wait(&empty[slot], ph ^ 1u, abort_flag)) { ok = false; break; }
+        if (!tc::bar_spin(&empty[slot], ph ^ 1u, abort_flag)) { ok = false; break; }
         bar_expect(&full[slot], chunk_bytes);
-        bulk_copy(ring + (size_t)slot * stage_bytes, Fs + j * slot_floats + (int64_t)c * 32 * mp8, chunk_bytes,
-                  &full[slot]);
+        bulk_copy(ring + (size_t)slot * stage_bytes, chunk_src(it), chunk_bytes, &full[slot]);
         issued = it + 1;
       }
       if (!ok) {
@@ -231,11 +245,11 @@ k_subst_x3(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, co
         const uint32_t d = tmem + (uint32_t)(st & 1) * X3_HALF;
         for (int c = 0; c < nck; ++c, ++it) {
           if ((c & 3) == 0) {   // the next 32 columns of V (this step's K range) are written
-            if (!tc::bar_wait(&aready[c >> 2], (uint32_t)(st & 1), abort_flag)) { ok = false; break; }
+            if (!tc::bar_spin(&aready[c >> 2], (uint32_t)(st & 1), abort_flag)) { ok = false; break; }
             tc::fence_after();
           }
           const int slot = (int)(it % NS);
-          if (!tc::bar_wait(&full[slot], (uint32_t)((it / NS) & 1), abort_flag)) { ok = false; break; }
+          if (!tc::bar_spin(&full[slot], (uint32_t)((it / NS) & 1), abort_flag)) { ok = false; break; }
           const uint32_t sb = tc::su32(ring + (size_t)slot * stage_bytes);
           const uint64_t da1 = tc::mdesc(a1 + (uint32_t)c * 2 * kX3Lbo, kX3Lbo, asbo);
           const uint64_t da2 = tc::mdesc(a2 + (uint32_t)c * 2 * kX3Lbo, kX3Lbo, asbo);
@@ -312,7 +326,23 @@ k_subst_x3(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, co
       const double2 c = nfwd ? pool[s.aoff + 2 * m + 1 + rows + jn] : pool[s.aoff + 2 * m + 1 + rows + jn + 1];
       cpl = make_float2((float)c.x, (float)c.y);
     }
-    const bool got = __all_sync(0xffffffffu, tc::bar_wait(dfull, (uint32_t)(st & 1), abort_flag));
+    float2 pre[X3_GROUPS][8];
+#pragma unroll
+    for (int g = 0; g < X3_GROUPS; ++g) {
+      const int k0 = 32 * g + coff;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) pre[g][i] = make_float2(0.f, 0.f);
+      if (g < ngrp && k0 < mp8) {
+        if (!fwd) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            if (live && k0 + i < m) pre[g][i] = stg[(int64_t)j * m + k0 + i];
+        } else if (has_next && nfwd) {
+          load_rho(s.ey0 + jn, k0, pre[g]);
+        }
+      }
+    }
+    const bool got = __all_sync(0xffffffffu, tc::bar_spin(dfull, (uint32_t)(st & 1), abort_flag));
     if (!got) {
       if (lane == 0) {
         *abort_flag = 1;
@@ -322,23 +352,11 @@ k_subst_x3(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, co
     }
     tc::fence_after();
     const uint32_t dcol = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(st & 1) * X3_HALF;
-    for (int g = 0; g < ngrp; ++g) {
+#pragma unroll
+    for (int g = 0; g < X3_GROUPS; ++g) {
+      if (g >= ngrp) break;
       const int k0 = 32 * g + coff;
       const bool colok = k0 < mp8;
-      // operands that do not depend on this step's product: the staged w_j (backward) or
-      // the next grid row's residual (forward, next step forward)
-      float2 pre[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) pre[i] = make_float2(0.f, 0.f);
-      if (colok) {
-        if (!fwd) {
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            if (live && k0 + i < m) pre[i] = stg[(int64_t)j * m + k0 + i];
-        } else if (has_next && nfwd) {
-          load_rho(s.ey0 + jn, k0, pre);
-        }
-      }
       float v[32];
       tmem_ld32(dcol + (uint32_t)(32 * g), v);   // warp-collective
       // hi + lo parts (lanes l, l ^ 8): keep 16 of the 32 columns
@@ -363,10 +381,10 @@ k_subst_x3(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, co
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
           const int a = k0 + i;
-          const float2 out = fwd ? y8[i] : csub(pre[i], y8[i]);
+          const float2 out = fwd ? y8[i] : csub(pre[g][i], y8[i]);
           if (live && a < m) stg[(int64_t)j * m + a] = out;
           const float2 lc = cmul(lA[a], cpl);   // L_{jn} or U_{jn} entry of row a (zero past m)
-          nv[i] = nfwd ? cfms(lc, out, pre[i]) : cmul(lc, out);
+          nv[i] = nfwd ? cfms(lc, out, pre[g][i]) : cmul(lc, out);
           if (a >= m) nv[i] = make_float2(0.f, 0.f);
         }
         if (has_next) put_v8(A1, A2, asbo, warp, sl, k0, nv);

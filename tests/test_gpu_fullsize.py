@@ -8,8 +8,8 @@ alone.  Corner, edge and interior boxes are sampled.  The full solve is checked
 through a property that holds at any size: its FP64 relative residual, formed on
 the CPU with the oracle's own operator.
 
-Tolerances as in test_gpu_parity: FP32 factors 2e-4 relative L2 per sampled
-box, TF32 tensor-core storage 3e-2.
+Tolerances as in test_gpu_parity: FP32 factors and the split-TF32 tensor-core
+storage 2e-4 relative L2 per sampled box, TF32 tensor-core storage 3e-2.
 """
 import numpy as np
 import pytest
@@ -76,21 +76,23 @@ def test_precond_4096_sampled_boxes():
     _check_boxes(wl, z, f, 2e-4)
 
 
-def test_precond_batching_tensor_cores_sampled_boxes():
-    """1984^2, 16x16 uneven boxes, tensor-core storage, 16 sources in one
-    application (the batching configuration's lockstep group): sampled boxes of
-    two of the sources."""
-    wl = W.make_workload("batching", nrhs=16)
+@pytest.mark.parametrize("tcore,nrhs,checked,tol", [(True, 16, (0, 15), 3e-2), ("x3", 40, (0, 31, 32, 39), 2e-4)])
+def test_precond_batching_tensor_cores_sampled_boxes(tcore, nrhs, checked, tol):
+    """1984^2, 16x16 uneven boxes, tensor-core storage, several sources in one
+    application (the batching configuration's lockstep group): sampled boxes of some of
+    the sources.  TF32 storage: 16 sources, one CTA group; split-TF32 (FP32-grade): 40
+    sources, a full group of 32 and a ragged one of 8."""
+    wl = W.make_workload("batching", nrhs=nrhs)
     s = HelmholtzDDM(wl.N, wl.npml, wl.omega, wl.c, wl.nbx, wl.nby, wl.overlap, precision="c64", cut_x=wl.cut_x,
-                     cut_y=wl.cut_y, tcore=True)
-    f = W.random_complex((16, wl.n, wl.n), seed=43)
-    _, _, need = B.hd_query_workspace(s.ctx, 16, 1)
+                     cut_y=wl.cut_y, tcore=tcore)
+    f = W.random_complex((nrhs, wl.n, wl.n), seed=43)
+    _, _, need = B.hd_query_workspace(s.ctx, nrhs, 1)
     s.scratch = torch.empty(need, dtype=torch.uint8, device="cuda")
     s.scratch_bytes = need
     z = s.apply_precond(torch.from_numpy(f)).cpu().numpy()
     s.close()
-    for k in (0, 15):
-        _check_boxes(wl, z[k], f[k], 3e-2)
+    for k in checked:
+        _check_boxes(wl, z[k], f[k], tol)
 
 
 def test_solve_4096_residual_from_oracle_operator():
