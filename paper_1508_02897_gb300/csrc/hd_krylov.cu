@@ -249,9 +249,11 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, i
 // The same dot products for few basis vectors (nk + self <= KM): every warp takes a
 // DFC/8-element slice of the block's elements for all vectors (instead of one vector
 // for all elements), so short Arnoldi cycles keep every warp loading; the eight
-// warps' double-single sums are combined in a fixed order.
+// warps' double-single sums are combined in a fixed order.  Three blocks per SM (80
+// registers): the kernel is latency-bound, and the third block's loads in flight are
+// worth more than the registers the compiler would spend on unrolling.
 template <int KM>
-__global__ void __launch_bounds__(256) k_dots_df_few(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk0,
+__global__ void __launch_bounds__(256, 3) k_dots_df_few(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk0,
                                                      const double2 *__restrict__ w_all, int64_t ldw, int64_t n,
                                                      double2 *__restrict__ partial_all, int G, int64_t ldp,
                                                      const int *__restrict__ skip, const int *__restrict__ live,
@@ -335,7 +337,7 @@ __host__ __device__ __forceinline__ double lazy_gamma(double w2) {
 // slot vout_r as float pairs and to y_r in FP64 (the preconditioner's input); optionally
 // normpart[r][blk] = block sum of |y_r|^2.
 template <bool NORM>
-__global__ void __launch_bounds__(DT) k_update_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
+__global__ void __launch_bounds__(DT, 4) k_update_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
                                                   const double2 *__restrict__ coef_all, int ldc,
                                                   const double *__restrict__ sc_all, const double2 *base_all,
                                                   double2 *y_all, int64_t ldy, float4 *__restrict__ vout_all,

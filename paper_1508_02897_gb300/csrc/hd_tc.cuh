@@ -53,17 +53,6 @@ __device__ __forceinline__ bool bar_spin(uint64_t *bar, uint32_t parity, volatil
   return false;
 }
 
-// The same wait for a thread whose warp shares its scheduler with working warps: it sleeps
-// about `ns` nanoseconds between polls instead of issuing a test every few cycles.
-__device__ __forceinline__ bool bar_nap(uint64_t *bar, uint32_t parity, volatile int *abort_flag, uint32_t ns) {
-  for (uint32_t it = 0; it < (kWaitLimit >> 4); ++it) {
-    if (bar_test(bar, parity)) return true;
-    __nanosleep(ns);
-    if ((it & 63u) == 63u && *abort_flag) return false;
-  }
-  return false;
-}
-
 // Shared-memory matrix descriptor of the no-swizzle K-major layout: start address,
 // leading byte offset (between core matrices adjacent along K), stride byte offset
 // (between 8-row groups along M or N), descriptor version 1.
