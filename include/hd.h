@@ -393,7 +393,9 @@ typedef struct {
 } hd_server_counters;
 
 /* Starts a server on CUDA device `device` with max_slots (1..64) concurrent
- * requests and a device memory budget in bytes. */
+ * requests and a device memory budget in bytes.  Requests allocate their device
+ * memory from a memory pool of the server's own that keeps up to the budget mapped
+ * between requests (released by hd_server_destroy). */
 int hd_server_create(hd_server **out, size_t hbm_budget_bytes, int32_t max_slots, int32_t device);
 
 /* Queues one solve: medium c_host (FP64 velocity, NY x NX), sources f_host

@@ -62,6 +62,10 @@ struct hd_server {
   std::map<uint64_t, std::shared_ptr<hd::Request>> live;   // submitted, not yet collected
   std::vector<std::thread> workers;
   uint64_t completed = 0;
+  // the requests' device memory: a pool of the server's own that keeps up to the budget
+  // mapped between requests (a release threshold of zero would hand it back to the
+  // driver at every synchronisation and map it again for the next request)
+  cudaMemPool_t pool = nullptr;
 };
 
 namespace hd {
@@ -118,10 +122,12 @@ static void run_request(hd_server *srv, Request &q, cudaStream_t st) {
     q.error = what + ": " + hd_last_error();
   };
   q.stats.assign(q.nrhs, hd_gmres_stats{});
+  auto dalloc = [&](void **p, size_t bytes) {
+    return srv->pool ? cudaMallocFromPoolAsync(p, bytes, srv->pool, st) : cudaMallocAsync(p, bytes, st);
+  };
   do {
-    if (cudaMallocAsync(&c_d, sizeof(double) * n, st) != cudaSuccess ||
-        cudaMallocAsync(&f_d, sizeof(double2) * n * B, st) != cudaSuccess ||
-        cudaMallocAsync(&x_d, sizeof(double2) * n * B, st) != cudaSuccess) {
+    if (dalloc(&c_d, sizeof(double) * n) != cudaSuccess || dalloc(&f_d, sizeof(double2) * n * B) != cudaSuccess ||
+        dalloc(&x_d, sizeof(double2) * n * B) != cudaSuccess) {
       fail(HD_ERR_OOM, "device vectors");
       break;
     }
@@ -134,8 +140,7 @@ static void run_request(hd_server *srv, Request &q, cudaStream_t st) {
     int rc = hd_setup_medium(&ctx, &q.grid, &dec, reinterpret_cast<const double *>(c_d), q.precision, st);
     if (rc) { fail(rc, "hd_setup_medium"); break; }
     hd_query_workspace(ctx, B, q.opts.restart, &fb, &kb, &sb);
-    if (cudaMallocAsync(&fac, fb, st) != cudaSuccess || cudaMallocAsync(&kws, kb, st) != cudaSuccess ||
-        cudaMallocAsync(&scr, sb, st) != cudaSuccess) {
+    if (dalloc(&fac, fb) != cudaSuccess || dalloc(&kws, kb) != cudaSuccess || dalloc(&scr, sb) != cudaSuccess) {
       fail(HD_ERR_OOM, "workspaces");
       break;
     }
@@ -225,6 +230,17 @@ int hd_server_create(hd_server **out, size_t hbm_budget_bytes, int32_t max_slots
   s->budget = hbm_budget_bytes;
   s->max_slots = max_slots;
   s->device = device;
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&s->pool, &props) == cudaSuccess) {
+    uint64_t keep = hbm_budget_bytes;
+    cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  } else {
+    s->pool = nullptr;   // fall back to the device's default pool
+    cudaGetLastError();
+  }
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker_main, s);
   *out = s;
   return HD_OK;
@@ -319,6 +335,7 @@ int hd_server_destroy(hd_server *s) {
   }
   s->cv_work.notify_all();
   for (auto &t : s->workers) t.join();   // admitted requests finish; queued ones are dropped
+  if (s->pool) cudaMemPoolDestroy(s->pool);   // every allocation was freed and synchronised by its worker
   delete s;
   return HD_OK;
 }
