@@ -343,8 +343,9 @@ int hd_block_gmres_solve(hd_ctx *ctx, const void *b_dev, void *x_dev, int32_t p,
  * z_dev (complex128 NY x NX, contents irrelevant, z is overwritten) with CUDA
  * events on `stream`, and keeps the fastest for this context.  The choice is
  * remembered for the process per (precision, storage layout, widest box,
- * number of boxes, device), so later contexts of the same shape reuse it without timing.
- * Needs a prior hd_factor_subdomains; synchronises `stream`.  Any output
+ * number of boxes, device), and hd_setup_medium applies a remembered choice to every
+ * later context of the same shape (no timing).  The server tunes the first request of
+ * each shape this way.  Needs a prior hd_factor_subdomains; synchronises `stream`.  Any output
  * pointer may be NULL; *ms_out is the winner's time per application (-1 when
  * taken from the cache). */
 int hd_autotune(hd_ctx *ctx, const void *r_dev, void *z_dev, void *scratch_dev, size_t scratch_bytes,

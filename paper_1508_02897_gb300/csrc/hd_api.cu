@@ -253,6 +253,7 @@ int hd_setup_medium(hd_ctx **out, const hd_grid *grid, const hd_decomp *dec, con
   if (e != cudaSuccess) { free_ctx(c); return cuda_fail(e, "hd_setup_medium status"); }
   if (status) { free_ctx(c); set_error("hd_setup_medium: velocity must be finite and positive"); return HD_ERR_NUMERIC; }
   c->t_launch[T_OTHER] += 3;  // the three table kernels above
+  lookup_tuning(c);   // a launch shape tuned earlier in this process for the same shape class
   *out = c;
   return HD_OK;
 }

@@ -320,6 +320,7 @@ constexpr int kMaxBoxWidthX3 = 176;
 cudaError_t launch_subst_x3(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec_stride, void *staging,
                             int64_t stg_stride, cudaStream_t st);
 size_t krylov_bytes(int64_t n, int restart, int nrhs);
+bool lookup_tuning(hd_ctx *ctx);
 int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st, int *ct_out,
                    int *ns_out, float *ms_out);
 int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const hd_gmres_opts *o, void *kws,

@@ -146,6 +146,10 @@ static void run_request(hd_server *srv, Request &q, cudaStream_t st) {
     }
     rc = hd_factor_subdomains(ctx, fac, fb, scr, sb, st);
     if (rc) { fail(rc, "hd_factor_subdomains"); break; }
+    // the substitution's launch shape: tuned once per shape class in this process (the first
+    // request of a class pays for the timing runs; f_d and x_d are free until the solve)
+    if (!lookup_tuning(ctx) && hd_autotune(ctx, f_d, x_d, scr, sb, nullptr, nullptr, nullptr, st) != HD_OK)
+      cudaGetLastError();
     int worst = HD_OK;
     for (int r0 = 0; r0 < q.nrhs; r0 += B) {
       const int g = std::min(B, q.nrhs - r0);

@@ -783,6 +783,21 @@ namespace hd {
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
+// Applies the launch shape an earlier autotune chose for this context's shape (same
+// precision, storage, widest box, box count and device) in this process; false if none.
+bool lookup_tuning(hd_ctx *ctx) {
+  if (ctx->tc) return true;   // the tensor-core substitution has one launch shape
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(ctx->prec, ctx->sym ? 1 : 0, ctx->max_m, ctx->nsub, dev);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune_cache.find(key);
+  if (it == g_tune_cache.end()) return false;
+  ctx->tune_ct = it->second.first;
+  ctx->tune_ns = it->second.second;
+  return true;
+}
+
 int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cudaStream_t st, int *ct_out,
                    int *ns_out, float *ms_out) {
   if (ctx->tc) {   // the tensor-core substitution has one launch shape (ring sized by shared memory)
