@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhd.so")
-UNITS = ["hd_api", "hd_stencil", "hd_factor", "hd_factor_tc", "hd_subst", "hd_subst_tc", "hd_subst_x3", "hd_krylov", "hd_block", "hd_noalloc", "hd_server"]
+UNITS = ["hd_api", "hd_stencil", "hd_factor", "hd_factor_tc", "hd_subst", "hd_subst_tc", "hd_subst_x3", "hd_krylov", "hd_gs", "hd_block", "hd_noalloc", "hd_server"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -394,7 +394,7 @@ k_factor(const SubDev *__restrict__ subs, const double2 *__restrict__ pool, cons
 template <typename R, typename S, int LAY>
 static cudaError_t launch_factor_rs(hd_ctx *ctx, void *factor, void *work, const int32_t *only, cudaStream_t st) {
   const size_t smem = factor_smem_bytes(ctx->prec, ctx->max_m);
-  cudaError_t e = cudaFuncSetAttribute(k_factor<R, S, LAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(k_factor<R, S, LAY>, smem);
   if (e != cudaSuccess) return e;
   k_factor<R, S, LAY><<<ctx->nsub, FT, smem, st>>>(ctx->d_subs, ctx->d_lpool, ctx->d_k2, ctx->NX, ctx->h * ctx->h,
                                              reinterpret_cast<S *>(factor), reinterpret_cast<C<R> *>(work),

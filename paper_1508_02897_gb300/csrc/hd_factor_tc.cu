@@ -622,7 +622,7 @@ k_factor_tc(const SubDev *__restrict__ subs, int nsub, const double2 *__restrict
 
 template <typename S, int LAY>
 static cudaError_t launch_tc(hd_ctx *ctx, void *factor, float tau2, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(k_factor_tc<S, LAY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  cudaError_t e = allow_smem(k_factor_tc<S, LAY>, kSmem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -61,6 +61,13 @@ template <typename T> __device__ __forceinline__ T cinv(T a) {
   auto d = fma_rn(a.x, a.x, mul_rn(a.y, a.y));
   return mk<T>(a.x / d, -a.y / d);
 }
+// Scale of the first Gram-Schmidt pass's output in the double-single mode: 1 / ||w|| from
+// the pass's self dot product ||w||^2 (1 when that is zero or not finite).  The stored
+// vector then has the norm ||w - V h|| / ||w|| <= 1 whatever the norms of earlier ones, so
+// lazily normalised magnitudes cannot compound over a restart cycle.
+__host__ __device__ __forceinline__ double lazy_gamma(double w2) {
+  return (w2 > 0.0 && w2 < 1.0e300) ? 1.0 / sqrt(w2) : 1.0;
+}
 // FP64 <-> float-pair conversions without conversion instructions, which on this GPU
 // issue at the FP64 pipe's rate (1/64 of FP32).  ds_split(x) = (h, l): h is x truncated
 // to 24 significant bits (its bits moved into float fields), l = x - h rounded to float.
@@ -289,6 +296,16 @@ int cuda_fail(cudaError_t e, const char *what);
     if (e_ != cudaSuccess) return ::hd::cuda_fail(e_, #call); \
   } while (0)
 
+// Dynamic shared memory: a kernel's limit is raised to the most the device allows it
+// (the opt-in maximum less its static shared memory), the same value on every call.
+// Server slots launch one kernel with different sizes from several host threads at once;
+// a limit set to each launch's own size would race (one thread lowering it between
+// another's set and launch).  Sizes above the device's maximum give cudaErrorInvalidValue.
+cudaError_t allow_smem_ptr(const void *kernel, size_t bytes);
+template <typename K> cudaError_t allow_smem(K *kernel, size_t bytes) {
+  return allow_smem_ptr(reinterpret_cast<const void *>(kernel), bytes);
+}
+
 // profiling brackets around a launch on `st`
 void tic(hd_ctx *ctx, int cls, cudaStream_t st);
 void toc(hd_ctx *ctx, int cls, cudaStream_t st, int nkernels);
@@ -325,6 +342,17 @@ int autotune_subst(hd_ctx *ctx, const double2 *r, double2 *z, void *staging, cud
                    int *ns_out, float *ms_out);
 int run_gmres_batch(hd_ctx *ctx, const double2 *b, double2 *x, int nrhs, const hd_gmres_opts *o, void *kws,
                     void *scratch, hd_gmres_stats *stats, cudaStream_t st);
+// Streaming double-single Gram-Schmidt passes (hd_gs.cu).  gs_items(n): work items (and
+// partial sums) per right-hand side; the dots take at most kGsDotsMax basis vectors.
+constexpr int kGsDotsMax = 12;
+int gs_items(int64_t n);
+cudaError_t launch_gs_dots(const float4 *V, int64_t ldv, int64_t ldvr, int nk0, const double2 *w, int64_t ldw,
+                           int64_t n, int B, double2 *partial, int64_t ldp, const int *skip, const int *live, int self,
+                           int32_t *status, cudaStream_t st);
+cudaError_t launch_gs_update(const float4 *V, int64_t ldv, int64_t ldvr, int nk, const double2 *coef, int ldc,
+                             const double *sc, const double2 *base, double2 *y, int64_t ldy, float4 *vout, int64_t n,
+                             int B, double2 *normpart, int64_t ldp, const int *skip, const int *live, int scale,
+                             int32_t *status, cudaStream_t st);
 size_t factor_smem_bytes(int prec, int max_m);
 // Block flexible GMRES (hd_block.cu)
 size_t block_krylov_bytes(int64_t n, int restart, int p);

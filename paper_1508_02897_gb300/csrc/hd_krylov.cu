@@ -246,197 +246,6 @@ __global__ void __launch_bounds__(256) k_dots_df(const float4 *__restrict__ V, i
   }
 }
 
-// The same dot products for few basis vectors (nk + self <= KM): every warp takes a
-// DFC/8-element slice of the block's elements for all vectors (instead of one vector
-// for all elements), so short Arnoldi cycles keep every warp loading; the eight
-// warps' double-single sums are combined in a fixed order.  Three blocks per SM (80
-// registers): the kernel is latency-bound, and the third block's loads in flight are
-// worth more than the registers the compiler would spend on unrolling.
-template <int KM>
-__global__ void __launch_bounds__(256, 3) k_dots_df_few(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk0,
-                                                     const double2 *__restrict__ w_all, int64_t ldw, int64_t n,
-                                                     double2 *__restrict__ partial_all, int G, int64_t ldp,
-                                                     const int *__restrict__ skip, const int *__restrict__ live,
-                                                     int self) {
-  __shared__ float4 red[8][KM];
-  if ((skip && skip[blockIdx.y]) || (live && !live[blockIdx.y])) return;
-  const int nk = nk0 + self;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t base = (int64_t)blockIdx.x * DFC;
-  const int cnt = (int)min((int64_t)DFC, n - base);
-  const double2 *w = w_all + (int64_t)blockIdx.y * ldw;
-  const float4 *Vr = V + (int64_t)blockIdx.y * ldvr;
-  double2 *partial = partial_all + (int64_t)blockIdx.y * ldp;
-  constexpr int U = DFC / 256;   // elements per lane
-  float4 wv[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int i = warp * (DFC / 8) + u * 32 + lane;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < cnt) {
-      const double2 x = w[base + i];
-      const float2 r = ds_split(x.x), m = ds_split(x.y);
-      v = make_float4(r.x, r.y, m.x, m.y);
-    }
-    wv[u] = v;
-  }
-#pragma unroll
-  for (int k = 0; k < KM; ++k) {
-    if (k >= nk) break;
-    const float4 *vk = Vr + (int64_t)k * ldv + base;
-    float4 vv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = warp * (DFC / 8) + u * 32 + lane;
-      vv[u] = i < cnt ? (k < nk0 ? vk[i] : wv[u]) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const float4 a = vv[u], b = wv[u];
-      ds_mac(rh, rl, a.x, a.y, b.x, b.y);     // re += ar br
-      ds_mac(rh, rl, a.z, a.w, b.z, b.w);     // re += ai bi
-      ds_mac(ih, il, a.x, a.y, b.z, b.w);     // im += ar bi
-      ds_mac(ih, il, -a.z, -a.w, b.x, b.y);   // im -= ai br
-    }
-    ds_renorm(rh, rl);
-    ds_renorm(ih, il);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float a = __shfl_xor_sync(0xffffffffu, rh, o), b = __shfl_xor_sync(0xffffffffu, rl, o);
-      const float c = __shfl_xor_sync(0xffffffffu, ih, o), d = __shfl_xor_sync(0xffffffffu, il, o);
-      ds_add(rh, rl, a, b);
-      ds_add(ih, il, c, d);
-    }
-    if (lane == 0) red[warp][k] = make_float4(rh, rl, ih, il);
-  }
-  __syncthreads();
-  if (tid < nk) {
-    float4 t = red[0][tid];
-    for (int q = 1; q < 8; ++q) {
-      const float4 o = red[q][tid];
-      ds_add(t.x, t.y, o.x, o.y);
-      ds_add(t.z, t.w, o.z, o.w);
-    }
-    partial[(int64_t)tid * G + blockIdx.x] = make_double2(ds_to_d(t.x, t.y), ds_to_d(t.z, t.w));
-  }
-}
-
-// Scale of the first Gram-Schmidt pass's output in the double-single mode: 1 / ||w|| from
-// the pass's self dot product ||w||^2 (1 when that is zero or not finite).  The stored
-// vector then has the norm ||w - V h|| / ||w|| <= 1 whatever the norms of earlier ones, so
-// lazily normalised magnitudes cannot compound over a restart cycle.
-__host__ __device__ __forceinline__ double lazy_gamma(double w2) {
-  return (w2 > 0.0 && w2 < 1.0e300) ? 1.0 / sqrt(w2) : 1.0;
-}
-
-// y_r = g_r (base_r - sum_k V_r[k] coef_r[k] sc_r[k]^2) (double-single accumulation): the
-// stored basis vectors are u_k = v_k / sc_k (normalised lazily, see k_arnoldi_step), so
-// the projection on v_k takes coef sc_k^2.  With `scale`, g_r = lazy_gamma(coef_r[nk]) =
-// 1 / ||base_r|| from the first pass's self dot product, else 1.  y_r goes to the basis
-// slot vout_r as float pairs and to y_r in FP64 (the preconditioner's input); optionally
-// normpart[r][blk] = block sum of |y_r|^2.
-template <bool NORM>
-__global__ void __launch_bounds__(DT, 4) k_update_df(const float4 *__restrict__ V, int64_t ldv, int64_t ldvr, int nk,
-                                                  const double2 *__restrict__ coef_all, int ldc,
-                                                  const double *__restrict__ sc_all, const double2 *base_all,
-                                                  double2 *y_all, int64_t ldy, float4 *__restrict__ vout_all,
-                                                  int64_t n, double2 *__restrict__ normpart_all, int64_t ldp,
-                                                  const int *__restrict__ skip, const int *__restrict__ live,
-                                                  int scale) {
-  extern __shared__ float4 csm[];  // [nk]
-  __shared__ double nsm[DT / 32];
-  __shared__ double gsm;
-  const int tid = threadIdx.x, r = blockIdx.y;
-  if ((skip && skip[r]) || (live && !live[r])) return;
-  const double2 *coef = coef_all + (int64_t)r * ldc;
-  const double *sc = sc_all + (int64_t)r * ldc;
-  const float4 *Vr = V + (int64_t)r * ldvr;
-  const double2 *base = base_all + (int64_t)r * ldy;
-  double2 *y = y_all + (int64_t)r * ldy;
-  float4 *vout = vout_all + (int64_t)r * ldvr;
-  // the output scale once per block (an FP64 square root and division)
-  if (tid == 0) gsm = scale ? lazy_gamma(coef[nk].x) : 1.0;
-  __syncthreads();
-  const double g = gsm;
-  const float2 gds = ds_split(g);
-  for (int k = tid; k < nk; k += DT) {
-    const double2 c0 = coef[k];
-    const double s2 = sc[k] * sc[k] * g;
-    const double2 c = make_double2(c0.x * s2, c0.y * s2);
-    float2 cr = ds_split(c.x), ci = ds_split(c.y);
-    csm[k] = make_float4(cr.x, cr.y, ci.x, ci.y);
-  }
-  __syncthreads();
-  constexpr int E = 4;
-  const int64_t b0 = (int64_t)blockIdx.x * DCHUNK + tid;
-  float nh = 0.f, nl = 0.f;   // double-single |y|^2 of this thread's elements
-#pragma unroll 1
-  for (int half = 0; half < DE / E; ++half) {
-    float rh[E], rl[E], ih[E], il[E];
-#pragma unroll
-    for (int e = 0; e < E; ++e) { rh[e] = rl[e] = ih[e] = il[e] = 0.f; }
-#pragma unroll 2
-    for (int k = 0; k < nk; ++k) {
-      const float4 c = csm[k];
-      const float4 *vk = Vr + (int64_t)k * ldv;
-      float4 a[E];
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        int64_t i = b0 + (int64_t)DT * (half * E + e);
-        a[e] = i < n ? vk[i] : make_float4(0.f, 0.f, 0.f, 0.f);
-      }
-#pragma unroll
-      for (int e = 0; e < E; ++e) {
-        ds_mac(rh[e], rl[e], a[e].x, a[e].y, c.x, c.y);      // re += ar cr
-        ds_mac(rh[e], rl[e], -a[e].z, -a[e].w, c.z, c.w);    // re -= ai ci
-        ds_mac(ih[e], il[e], a[e].x, a[e].y, c.z, c.w);      // im += ar ci
-        ds_mac(ih[e], il[e], a[e].z, a[e].w, c.x, c.y);      // im += ai cr
-      }
-      if ((k & 7) == 7) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) { ds_renorm(rh[e], rl[e]); ds_renorm(ih[e], il[e]); }
-      }
-    }
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      int64_t i = b0 + (int64_t)DT * (half * E + e);
-      if (i < n) {
-        // y = g base - acc in double-single (g base as a double-single product: no FP64
-        // multiply), then one FP64 add per component
-        const double2 bv = base[i];
-        const float2 br = ds_split(bv.x), bi = ds_split(bv.y);
-        float oh = 0.f, ol = 0.f, qh = 0.f, ql = 0.f;
-        ds_mac(oh, ol, gds.x, gds.y, br.x, br.y);
-        ds_mac(qh, ql, gds.x, gds.y, bi.x, bi.y);
-        ds_renorm(oh, ol);
-        ds_renorm(qh, ql);
-        ds_add(oh, ol, -rh[e], -rl[e]);
-        ds_add(qh, ql, -ih[e], -il[e]);
-        y[i] = make_double2(ds_to_d(oh, ol), ds_to_d(qh, ql));
-        vout[i] = make_float4(oh, ol, qh, ql);
-        if (NORM) {
-          ds_mac(nh, nl, oh, ol, oh, ol);
-          ds_mac(nh, nl, qh, ql, qh, ql);
-        }
-      }
-    }
-    if (NORM) ds_renorm(nh, nl);
-  }
-  if (NORM) {
-    double nrm = ds_to_d(nh, nl);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
-    if ((tid & 31) == 0) nsm[tid >> 5] = nrm;
-    __syncthreads();
-    if (tid == 0) {
-      double s = 0.0;
-      for (int q = 0; q < DT / 32; ++q) s += nsm[q];
-      normpart_all[(int64_t)r * ldp + blockIdx.x] = make_double2(s, 0.0);
-    }
-  }
-}
-
 // v_r = w_r * red[4 r + 1].x written twice: split into V (double-single) and FP64 into vin
 // (the normalised first vector of each restart cycle; later ones are stored lazily).
 // SCE elements per thread with all loads issued first (one element per thread left too
@@ -700,37 +509,29 @@ struct Krylov {
   }
   cudaError_t dots_df(int nk, const double2 *x, double2 *out, int ldo, const int *skip = nullptr, int self = 0) {
     tic(ctx, T_ARNOLDI, st);
-    const dim3 grid(L.Gdf, B);
-    if (nk + self <= 4)
-      k_dots_df_few<4><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, live,
-                                                 self);
-    else if (nk + self <= 8)
-      k_dots_df_few<8><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, live,
-                                                 self);
-    else if (nk + self <= 12)
-      k_dots_df_few<12><<<grid, 256, 0, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip, live,
-                                                 self);
-    else
-      k_dots_df<<<grid, 256, sizeof(float4) * DFC, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf, ldp(), skip,
-                                                         live, self);
-    k_reduce<<<dim3(nk + self, B), 256, 0, st>>>(part(), L.Gdf, ldp(), out, ldo, skip, 1);
+    int G = L.Gdf;
+    if (nk <= kGsDotsMax) {   // streamed through a shared-memory ring (hd_gs.cu)
+      G = gs_items(L.n);
+      const cudaError_t e = launch_gs_dots(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, B, part(), ldp(), skip, live, self,
+                                           ctx->d_status, st);
+      if (e != cudaSuccess) return e;
+    } else {
+      k_dots_df<<<dim3(L.Gdf, B), 256, sizeof(float4) * DFC, st>>>(Vdf(), L.n, ldvr(), nk, x, L.n, L.n, part(), L.Gdf,
+                                                                   ldp(), skip, live, self);
+    }
+    k_reduce<<<dim3(nk + self, B), 256, 0, st>>>(part(), G, ldp(), out, ldo, skip, 1);
     toc(ctx, T_ARNOLDI, st, 2);
     return cudaGetLastError();
   }
-  // y = base - V (coef sc^2) into vin (FP64) and into basis slot nk (float pairs)
+  // y = g (base - V (coef sc^2)) into vin (FP64) and into basis slot nk (float pairs)
   cudaError_t update_df(int nk, const double2 *coef, int ldc, const double *sc, const double2 *base,
                         double2 *norm_out, int scale, const int *skip = nullptr) {
     tic(ctx, T_ARNOLDI, st);
-    size_t sm = sizeof(float4) * nk;
     float4 *vout = Vdf() + (int64_t)nk * L.n;
-    if (norm_out) {
-      k_update_df<true><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, sc, base, vin(), L.n, vout,
-                                                      L.n, part(), ldp(), skip, live, scale);
-      k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), L.G, ldp(), norm_out, 4, skip, 2);
-    } else {
-      k_update_df<false><<<dim3(L.G, B), DT, sm, st>>>(Vdf(), L.n, ldvr(), nk, coef, ldc, sc, base, vin(), L.n, vout,
-                                                       L.n, nullptr, 0, skip, live, scale);
-    }
+    const cudaError_t e = launch_gs_update(Vdf(), L.n, ldvr(), nk, coef, ldc, sc, base, vin(), L.n, vout, L.n, B,
+                                           norm_out ? part() : nullptr, ldp(), skip, live, scale, ctx->d_status, st);
+    if (e != cudaSuccess) return e;
+    if (norm_out) k_reduce<<<dim3(1, B), 256, 0, st>>>(part(), gs_items(L.n), ldp(), norm_out, 4, skip, 2);
     toc(ctx, T_ARNOLDI, st, norm_out ? 2 : 1);
     return cudaGetLastError();
   }

@@ -625,7 +625,7 @@ static cudaError_t launch_subst(hd_ctx *ctx, const double2 *r, int nrhs, int64_t
   const int groups = (nrhs + NR - 1) / NR;
   const int ns = (NR == 1 && ctx->tune_ns > 0) ? ctx->tune_ns : ring_stages<T, S>(ctx, ldmax, NR, groups);
   const size_t smem = subst_smem<T, S>(ns, ldmax, NR);
-  cudaError_t e = cudaFuncSetAttribute(k_subst<R, S, CT, NA, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(k_subst<R, S, CT, NA, NR>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(groups, ctx->nsub);   // a box's source groups run side by side and share its factor reads in L2
   k_subst<R, S, CT, NA, NR><<<grid, CT + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,
@@ -662,7 +662,7 @@ static cudaError_t launch_subst_sym(hd_ctx *ctx, const double2 *r, int nrhs, int
   int ns = ctx->tune_ns > 0 && NR == 1 ? ctx->tune_ns : (budget > fixed ? (int)((budget - fixed) / (stage + 16)) : 2);
   ns = std::min(32, std::max(2, ns));
   const size_t smem = subst_sym_smem<T, S>(ns, mpmax, NW, NR, ntmax);
-  cudaError_t e = cudaFuncSetAttribute(k_subst_sym<R, S, NW, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(k_subst_sym<R, S, NW, NR>, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(groups, ctx->nsub);   // a box's source groups run side by side and share its factor reads in L2
   k_subst_sym<R, S, NW, NR><<<grid, NW * 32 + 32, smem, st>>>(ctx->d_subs, ctx->d_lpool,

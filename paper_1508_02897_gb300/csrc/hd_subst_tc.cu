@@ -393,7 +393,7 @@ cudaError_t launch_subst_tc(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec
   int ns = 2;
   while (ns < 16 && subst_tc_smem(ns + 1, mp8max) <= budget) ++ns;
   const size_t smem = subst_tc_smem(ns, mp8max);
-  cudaError_t e = cudaFuncSetAttribute(k_subst_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(k_subst_tc, smem);
   if (e != cudaSuccess) return e;
   // the groups of one box are neighbours in launch order: they run together and read
   // the box's factor chunks at about the same time, so L2 serves most repeated reads

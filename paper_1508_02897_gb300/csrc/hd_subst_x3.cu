@@ -414,7 +414,7 @@ cudaError_t launch_subst_x3(hd_ctx *ctx, const double2 *r, int nrhs, int64_t vec
   size_t smem = subst_x3_smem(ns, mp8max);
   if (smem > (size_t)optin) return cudaErrorInvalidValue;
   smem = std::max(smem, (size_t)optin / 2 + 1024);   // keeps a second CTA off the SM
-  cudaError_t e = cudaFuncSetAttribute(k_subst_x3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_smem(k_subst_x3, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(groups, ctx->nsub);
   k_subst_x3<<<grid, X3_THREADS, smem, st>>>(ctx->d_subs, ctx->d_lpool, reinterpret_cast<const float *>(ctx->factor),
