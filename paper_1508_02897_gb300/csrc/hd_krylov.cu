@@ -329,66 +329,69 @@ __global__ void k_cycle_init(GmresDev d) {
 // the second (if any) h2_k = u_k^H of that and stored y = g (A z_j - sum_k h_kj v_k) / sc_j;
 // hence h_kj = sc_j sc_k (h1_k + h2_k / g), h_{j+1,j} = sc_j ||y|| / g and
 // sc_{j+1} = 1 / ||y||.
+// The column is formed and rotated in registers (each entry computed from h1 and h2 when
+// the rotation reaches it, the rotated lower entry carried to the next rotation) and
+// stored once: one thread per right-hand side runs this chain, and a store and reload of
+// every entry through global memory would set its length.
 __global__ void k_arnoldi_step(GmresDev d, int j) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= d.nrhs || !d.live[r]) return;
   double2 *Hj = d.H + ((int64_t)r * d.restart + j) * d.ldh;
   const double2 *h1 = d.h1 + (int64_t)r * d.ldh, *h2 = d.h2 + (int64_t)r * d.ldh;
   double *cs = d.cs + (int64_t)r * d.restart;
-  {
-    const double nrm = sqrt(d.red[4 * r].x);
-    d.red[4 * r + 1] = make_double2(nrm > 0.0 ? 1.0 / nrm : 0.0, 0.0);   // for k_scale
-  }
+  double hn = sqrt(d.red[4 * r].x);
+  d.red[4 * r + 1] = make_double2(hn > 0.0 ? 1.0 / hn : 0.0, 0.0);   // for k_scale
   double2 *sn = d.sn + (int64_t)r * d.restart;
   double2 *g = d.g + (int64_t)r * d.ldh;
-  double hn = sqrt(d.red[4 * r].x);
+  double *sc = d.sc + (int64_t)r * d.ldh;
+  double sj = 1.0, ginv = 1.0;
   if (d.lazy) {
-    double *sc = d.sc + (int64_t)r * d.ldh;
-    const double sj = sc[j], g = lazy_gamma(h1[j + 1].x);
-    for (int i = 0; i <= j; ++i) {
-      const double2 h = make_double2(h1[i].x + h2[i].x / g, h1[i].y + h2[i].y / g);
-      const double f = sj * sc[i];
-      Hj[i] = make_double2(f * h.x, f * h.y);
-    }
+    sj = sc[j];
+    ginv = 1.0 / lazy_gamma(h1[j + 1].x);
     sc[j + 1] = hn > 0.0 ? 1.0 / hn : 0.0;
-    hn *= sj / g;
-  } else {
-    for (int i = 0; i <= j; ++i) Hj[i] = cadd(h1[i], h2[i]);
+    hn *= sj * ginv;
   }
-  Hj[j + 1] = make_double2(hn, 0.0);
+  // entry i of the new column: h1 + h2, or (lazy) sc_j sc_i (h1 + h2 / g)
+  auto col = [&](int i) -> double2 {
+    if (!d.lazy) return cadd(h1[i], h2[i]);
+    const double f = sj * sc[i];
+    return make_double2(f * (h1[i].x + h2[i].x * ginv), f * (h1[i].y + h2[i].y * ginv));
+  };
+  // the earlier rotations, applied in order to (a, b) = (H_ij, H_{i+1,j})
+  double2 a = col(0);
   for (int i = 0; i < j; ++i) {
-    double c = cs[i];
-    double2 s = sn[i];
-    double2 a = Hj[i], b = Hj[i + 1];
+    const double c = cs[i];
+    const double2 s = sn[i];
+    const double2 b = col(i + 1);
     double2 t0 = make_double2(c * a.x, c * a.y);
     t0 = cfma(s, b, t0);
-    double2 sc = make_double2(-s.x, s.y);               // -conj(s)
-    double2 t1 = cmul(sc, a);
+    const double2 msc = make_double2(-s.x, s.y);   // -conj(s)
+    double2 t1 = cmul(msc, a);
     t1 = make_double2(t1.x + c * b.x, t1.y + c * b.y);
     Hj[i] = t0;
-    Hj[i + 1] = t1;
+    a = t1;
   }
-  double2 a = Hj[j], b = Hj[j + 1];
-  double aa = cabs_(a), bb = cabs_(b), c;
+  // the new rotation zeroes H_{j+1,j} = hn
+  const double2 b = make_double2(hn, 0.0);
+  const double aa = cabs_(a), bb = cabs_(b);
+  double c;
   double2 s;
   if (bb == 0.0) {
     c = 1.0; s = make_double2(0.0, 0.0);
   } else if (aa == 0.0) {
     c = 0.0; s = make_double2(b.x / bb, -b.y / bb);
   } else {
-    double t = hypot(aa, bb);
+    const double t = hypot(aa, bb);
     c = aa / t;
-    double2 ph = make_double2(a.x / aa, a.y / aa);
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
     s = cmul(ph, make_double2(b.x / t, -b.y / t));
   }
   cs[j] = c;
   sn[j] = s;
-  double2 nj = make_double2(c * a.x, c * a.y);
-  Hj[j] = cfma(s, b, nj);
+  Hj[j] = cfma(s, b, make_double2(c * a.x, c * a.y));
   Hj[j + 1] = make_double2(0.0, 0.0);
-  double2 gj = g[j];
-  double2 sc = make_double2(-s.x, s.y);
-  g[j + 1] = cmul(sc, gj);
+  const double2 gj = g[j];
+  g[j + 1] = cmul(make_double2(-s.x, s.y), gj);
   g[j] = make_double2(c * gj.x, c * gj.y);
   double *stat = d.stat + 4 * r;
   stat[0] = cabs_(g[j + 1]);
