@@ -547,54 +547,114 @@ template <typename R> __device__ __forceinline__ R smooth_beta(int x, const Axis
 // The sum runs in the compute precision of the local solutions (FP32 for the c64
 // modes: one conversion per cell instead of one per contribution, since the FP64
 // pipe is the scarce one on this GPU) and is written out as complex128.
+//
+// A block covers 256 consecutive cells of GR grid rows.  The boxes that can cover them
+// (per row: the boxes whose extent holds the row; per column: box columns nearx - 1 ..
+// nearx + 1 of each cell) are looked up once per block into shared memory with their
+// staging row offsets, so a thread's staging loads for its GR cells are independent
+// (no chain of table, box and staging loads per cell).  Contributions are added in the
+// same order as a per-cell walk (box rows, then box columns, ascending): the result does
+// not depend on the blocking.  A span with more candidate box columns than GXC (boxes
+// under about 40 cells wide) takes the per-cell walk.
+constexpr int GR = 4, GXC = 8;
 template <typename R, bool SMOOTH>
 __global__ void __launch_bounds__(256)
 k_gather(const SubDev *__restrict__ subs, const AxisDev *__restrict__ axx, const AxisDev *__restrict__ axy,
          const int32_t *__restrict__ nearx, const int32_t *__restrict__ neary, int nbx, int nby,
          const C<R> *__restrict__ staging_all, int64_t stg_stride, double2 *__restrict__ z_all, int64_t vec_stride,
-         int NX) {
-  __shared__ int ylist[3], yoff[3], ny_s;
-  __shared__ R ybeta[3];
-  const int gy = blockIdx.y;
-  if (threadIdx.x == 0) {
+         int NX, int NY) {
+  __shared__ int ylist[GR][3], yoff[GR][3], ny_s[GR];
+  __shared__ R ybeta[GR][3];
+  __shared__ AxisDev xax[GXC];
+  __shared__ int xj[GXC], ncx;
+  __shared__ int64_t rowbase[GR][3][GXC];   // staging offset of (row, box row q, candidate c), less e0 of c
+  const int t = threadIdx.x;
+  const int gx0 = blockIdx.x * 256, gy0 = blockIdx.y * GR;
+  if (t < GR) {
     // boxes whose extent covers grid row gy (at most 3, in practice 1 or 2)
-    const int iy = neary[gy];
+    const int gy = gy0 + t;
     int cnt = 0;
-    for (int jy = max(iy - 1, 0); jy <= min(iy + 1, nby - 1); ++jy) {
-      const AxisDev ay = axy[jy];
-      if (gy >= ay.e0 && gy < ay.e1) {
-        ylist[cnt] = jy;
-        yoff[cnt] = gy - ay.e0;
-        if (SMOOTH) ybeta[cnt] = smooth_beta<R>(gy, ay);
-        ++cnt;
+    if (gy < NY) {
+      const int iy = neary[gy];
+      for (int jy = max(iy - 1, 0); jy <= min(iy + 1, nby - 1); ++jy) {
+        const AxisDev ay = axy[jy];
+        if (gy >= ay.e0 && gy < ay.e1) {
+          ylist[t][cnt] = jy;
+          yoff[t][cnt] = gy - ay.e0;
+          if (SMOOTH) ybeta[t][cnt] = smooth_beta<R>(gy, ay);
+          ++cnt;
+        }
       }
     }
-    ny_s = cnt;
+    ny_s[t] = cnt;
+  } else if (t == 32) {
+    // candidate box columns of the block's cells, ascending
+    const int gx1 = min(gx0 + 256, NX) - 1;
+    const int jlo = max(nearx[gx0] - 1, 0), jhi = min(nearx[gx1] + 1, nbx - 1);
+    int c = 0;
+    for (int jx = jlo; jx <= jhi; ++jx) {
+      const AxisDev ax = axx[jx];
+      if (ax.e1 <= gx0 || ax.e0 > gx1) continue;
+      if (c == GXC) { c = -1; break; }
+      xax[c] = ax;
+      xj[c] = jx;
+      ++c;
+    }
+    ncx = c;
   }
   __syncthreads();
-  const int gx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nc = ncx;
+  if (nc >= 0) {
+    for (int k = t; k < GR * 3 * GXC; k += 256) {
+      const int row = k / (3 * GXC), q = (k / GXC) % 3, c = k % GXC;
+      if (q < ny_s[row] && c < nc) {
+        const AxisDev ax = xax[c];
+        rowbase[row][q][c] = subs[ylist[row][q] * nbx + xj[c]].soff + (int64_t)yoff[row][q] * (ax.e1 - ax.e0) - ax.e0;
+      }
+    }
+  }
+  __syncthreads();
+  const int gx = gx0 + t;
   if (gx >= NX) return;
   const C<R> *staging = staging_all + (int64_t)blockIdx.z * stg_stride;
   double2 *z = z_all + (int64_t)blockIdx.z * vec_stride;
   const int ix = nearx[gx];
   const int jx0 = max(ix - 1, 0), jx1 = min(ix + 1, nbx - 1);
-  C<R> acc = mk<C<R>>(0, 0);
-  for (int q = 0; q < ny_s; ++q) {
-    const int jy = ylist[q], ry = yoff[q];
-    for (int jx = jx0; jx <= jx1; ++jx) {
-      const AxisDev ax = axx[jx];
-      if (gx < ax.e0 || gx >= ax.e1) continue;
-      const int ex = ax.e1 - ax.e0;
-      const C<R> v = staging[subs[jy * nbx + jx].soff + (int64_t)ry * ex + (gx - ax.e0)];
-      if (SMOOTH) {   // beta_ij u_ij (Remark after Eq. (pc))
-        const R b = mul_rn(ybeta[q], smooth_beta<R>(gx, ax));
-        acc = mk<C<R>>(fma_rn(b, v.x, acc.x), fma_rn(b, v.y, acc.y));
-      } else {
-        acc = cadd(acc, v);
+#pragma unroll
+  for (int row = 0; row < GR; ++row) {
+    const int gy = gy0 + row;
+    if (gy >= NY) break;
+    C<R> acc = mk<C<R>>(0, 0);
+    for (int q = 0; q < ny_s[row]; ++q) {
+      if (nc >= 0) {
+        for (int c = 0; c < nc; ++c) {
+          const AxisDev ax = xax[c];
+          if (xj[c] < jx0 || xj[c] > jx1 || gx < ax.e0 || gx >= ax.e1) continue;
+          const C<R> v = staging[rowbase[row][q][c] + gx];
+          if (SMOOTH) {   // beta_ij u_ij (Remark after Eq. (pc))
+            const R b = mul_rn(ybeta[row][q], smooth_beta<R>(gx, ax));
+            acc = mk<C<R>>(fma_rn(b, v.x, acc.x), fma_rn(b, v.y, acc.y));
+          } else {
+            acc = cadd(acc, v);
+          }
+        }
+      } else {   // per-cell walk
+        const int jy = ylist[row][q], ry = yoff[row][q];
+        for (int jx = jx0; jx <= jx1; ++jx) {
+          const AxisDev ax = axx[jx];
+          if (gx < ax.e0 || gx >= ax.e1) continue;
+          const C<R> v = staging[subs[jy * nbx + jx].soff + (int64_t)ry * (ax.e1 - ax.e0) + (gx - ax.e0)];
+          if (SMOOTH) {
+            const R b = mul_rn(ybeta[row][q], smooth_beta<R>(gx, ax));
+            acc = mk<C<R>>(fma_rn(b, v.x, acc.x), fma_rn(b, v.y, acc.y));
+          } else {
+            acc = cadd(acc, v);
+          }
+        }
       }
     }
+    z[(int64_t)gy * NX + gx] = make_double2((double)acc.x, (double)acc.y);
   }
-  z[(int64_t)gy * NX + gx] = make_double2((double)acc.x, (double)acc.y);
 }
 
 // Ring depth: as deep as shared memory allows for the CTAs that share an SM.
@@ -695,12 +755,12 @@ static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, dou
                         : launch_subst_sym_nr<R, S, 8>(ctx, r, nrhs, rs, staging, ctx->staging_elems, st);
     toc(ctx, T_SUBST, st, 1);
     if (e != cudaSuccess) return e;
-    dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
+    dim3 grid((ctx->NX + 255) / 256, (ctx->NY + GR - 1) / GR, nrhs);
     tic(ctx, T_GATHER, st);
     auto gather = ctx->smooth ? k_gather<R, true> : k_gather<R, false>;
     gather<<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
                                       ctx->nby, reinterpret_cast<const C<R> *>(staging), ctx->staging_elems, z, zs,
-                                      ctx->NX);
+                                      ctx->NX, ctx->NY);
     toc(ctx, T_GATHER, st, 1);
     return cudaGetLastError();
   }
@@ -717,12 +777,12 @@ static cudaError_t launch_apply_r(hd_ctx *ctx, const double2 *r, int64_t rs, dou
   }
   toc(ctx, T_SUBST, st, 1);
   if (e != cudaSuccess) return e;
-  dim3 grid((ctx->NX + 255) / 256, ctx->NY, nrhs);
+  dim3 grid((ctx->NX + 255) / 256, (ctx->NY + GR - 1) / GR, nrhs);
   tic(ctx, T_GATHER, st);
   auto gather = ctx->smooth ? k_gather<R, true> : k_gather<R, false>;
   gather<<<grid, 256, 0, st>>>(ctx->d_subs, ctx->d_axx, ctx->d_axy, ctx->d_nearx, ctx->d_neary, ctx->nbx,
                                     ctx->nby, reinterpret_cast<const C<R> *>(staging), ctx->staging_elems, z, zs,
-                                    ctx->NX);
+                                    ctx->NX, ctx->NY);
   toc(ctx, T_GATHER, st, 1);
   return cudaGetLastError();
 }
