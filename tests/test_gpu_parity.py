@@ -115,17 +115,20 @@ def test_precond_literal_ownership():
 @pytest.mark.parametrize("name", ["tiny", "ragged"])
 @pytest.mark.parametrize("arnoldi", ["fp64", "ds"])
 @pytest.mark.parametrize("reorth", ["always", "selective"])
-def test_gmres_fixed_steps_c128(name, arnoldi, reorth):
+@pytest.mark.parametrize("restart,k", [(3, 4), (10, 10)])
+def test_gmres_fixed_steps_c128(name, arnoldi, reorth, restart, k):
     """Same FGMRES variant on both sides: the iterate after k steps agrees
     (FP64 Gram-Schmidt, and the double-single one whose basis carries ~48 bits;
-    two passes always, or the second only after a cancellation)."""
+    two passes always, or the second only after a cancellation).  A 10-step cycle
+    runs the double-single dot kernel's 4-, 8- and 12-vector classes and the steps
+    whose chunks hold more tiles than the ring has stages."""
     case, c, g, A, P = oracle(name)
     s = gpu(name, "c128")
     f = W.gaussian_source(case["N"], case["npml"], 0.45, 0.55, 2.0 / case["N"])
     b = rhs_from_source(g, f)
-    k = 4
-    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=3, rtol=1e-15, max_iters=k, reorth=reorth)
-    x, st = s.solve(torch.from_numpy(b), restart=3, rtol=1e-15, max_iters=k, arnoldi=arnoldi, reorth=reorth)
+    ref = fgmres(lambda v: A @ v, lambda v: P.apply(v).ravel(), b, restart=restart, rtol=1e-15, max_iters=k,
+                 reorth=reorth)
+    x, st = s.solve(torch.from_numpy(b), restart=restart, rtol=1e-15, max_iters=k, arnoldi=arnoldi, reorth=reorth)
     assert st[0]["iters"] == ref.iters == k
     assert rel(x.cpu().numpy(), ref.x.reshape(g.n, g.n)) < 1e-9
 
